@@ -1,0 +1,253 @@
+"""Preconditioners B for the oracle.
+
+The flexible methods accept any, possibly nonlinear, map v -> B(v)
+(Sec. 2 and the notation table of Sec. 3).  The ones used here:
+
+* ``IdentityPC``      -- B(v) = v.
+* ``JacobiPC``        -- B(v) = D^-1 v, D = diag(A) (the block-Jacobi limit
+                         of one cell per block, Sec. 6).
+* ``InnerPCG``        -- k iterations of Jacobi-preconditioned CG (Alg. 3 with
+                         M^-1 = D^-1), zero initial guess, no tolerance test.
+                         Sec. 6 uses 5 such inner iterations per block; this is
+                         nonlinear in v, hence a flexible preconditioner.
+* ``Chebyshev``       -- k Chebyshev-Jacobi sweeps on D^-1 A over [lo, hi]
+                         (Saad, Iterative Methods for Sparse Linear Systems,
+                         2nd ed., Alg. 12.1), zero initial guess.
+* ``NoisyPC``         -- B(r) = r + eta ||r|| xi / ||xi|| with Gaussian xi,
+                         the pathological preconditioner of Fig. FCGtoy.
+* ``DensePC``         -- B(v) = M v for a given matrix (e.g. A^-1).
+
+Reduced-precision copies (``precision='fp32'`` / ``'bf16'``) emulate the
+mixed-precision preconditioners: the preconditioner's copy of A stores the
+diagonal, the interior face coefficients and D^-1, each rounded
+FP64 -> FP32 (-> BF16, round to nearest even); constant advection weights stay
+FP32; vector arithmetic is FP32; inner products are accumulated in FP64 from
+the FP32 values.  The paper fixes no reduced-precision arithmetic, so these
+are "parity unpinned" (checked by tolerance only).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .operators import StencilOperator, _shift
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round FP32 values to BF16 (round to nearest, ties to even), returned as FP32.
+
+    Works on the bit pattern: add 0x7FFF plus the lowest kept bit, then clear the
+    16 low bits.  NaN stays NaN.
+    """
+    f = np.asarray(x, dtype=np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    r = ((bits + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    out = r.view(np.float32).copy()
+    nan = np.isnan(f)
+    out[nan] = np.float32(np.nan)
+    return out
+
+
+def round_coefficients(x64: np.ndarray, precision: str) -> np.ndarray:
+    x32 = np.asarray(x64, dtype=np.float64).astype(np.float32)
+    if precision == "fp32":
+        return x32
+    if precision == "bf16":
+        return bf16_round(x32)
+    raise ValueError(precision)
+
+
+class RoundedStencil:
+    """The preconditioner's reduced-precision copy of a stencil operator.
+
+    y = d u - sum_interior K_f u_nbr - sum_d a_d u_up, with d, K_f rounded per
+    ``precision`` and a_d = h |v_d| in FP32; arithmetic in FP32.
+    """
+
+    def __init__(self, op: StencilOperator, precision: str):
+        self.op = op
+        self.shape = op.shape
+        self.d = round_coefficients(op.diagonal(), precision).reshape(op.shape)
+        self.dinv = round_coefficients(1.0 / op.diagonal(), precision).reshape(op.shape)
+        self.K = {}
+        for key, k in op.K.items():
+            dd, s = key
+            inside = _shift(np.ones(op.shape), op.axes[dd], s) > 0
+            self.K[key] = np.where(inside, round_coefficients(k, precision).reshape(op.shape),
+                                   np.float32(0.0)).astype(np.float32)
+        self.adv = [np.float32(a) for a in op.adv]
+
+    def apply(self, u32: np.ndarray) -> np.ndarray:
+        u = np.asarray(u32, dtype=np.float32).reshape(self.shape)
+        y = self.d * u
+        for (dd, s), k in self.K.items():
+            y = y - k * _shift(u, self.op.axes[dd], s)
+        for dd, ax in enumerate(self.op.axes):
+            v = self.op.vel[dd]
+            if v != 0.0:
+                up = -1 if v > 0 else +1
+                y = y - self.adv[dd] * _shift(u, ax, up)
+        return y.reshape(-1).astype(np.float32)
+
+
+def _dot(a, b) -> float:
+    return float(np.dot(np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)))
+
+
+class IdentityPC:
+    linear = True
+
+    def __call__(self, v):
+        return np.array(v, dtype=np.float64, copy=True)
+
+
+class JacobiPC:
+    linear = True
+
+    def __init__(self, A):
+        self.dinv = 1.0 / A.diagonal()
+
+    def __call__(self, v):
+        return self.dinv * np.asarray(v, dtype=np.float64)
+
+
+class DensePC:
+    linear = True
+
+    def __init__(self, m):
+        self.m = np.asarray(m, dtype=np.float64)
+
+    def __call__(self, v):
+        return self.m @ np.asarray(v, dtype=np.float64)
+
+
+class NoisyPC:
+    """B(r) = r + eta ||r|| xi_j / ||xi_j||, xi_j the j-th row of a noise bank."""
+
+    linear = False
+
+    def __init__(self, eta: float, bank: np.ndarray):
+        self.eta = float(eta)
+        self.bank = np.asarray(bank, dtype=np.float64)
+        self.calls = 0
+
+    def __call__(self, r):
+        xi = self.bank[self.calls % len(self.bank)]
+        self.calls += 1
+        r = np.asarray(r, dtype=np.float64)
+        return r + self.eta * np.linalg.norm(r) * xi / np.linalg.norm(xi)
+
+
+class InnerPCG:
+    """B(v) = x_k, k iterations of Alg. 3 (PCG, M^-1 = D^-1) on A x = v from x_0 = 0.
+
+    Loop body as in Alg. 3: x_i = x_{i-1} + alpha p; r_i = r_{i-1} - alpha s;
+    u_i = M^-1 r_i; gamma_i = <u_i, r_i>; beta_i = gamma_i / gamma_{i-1};
+    p_i = u_i + beta_i p_{i-1}; s_i = A p_i; eta_i = <s_i, p_i>;
+    alpha_i = gamma_i / eta_i.  After the k-th update of x the remaining
+    statements of that iteration are not needed and are skipped.
+    Guards: if gamma or eta is exactly zero, the current x is returned.
+    """
+
+    linear = False
+
+    def __init__(self, A, k: int, precision: str = "fp64"):
+        self.A = A
+        self.k = int(k)
+        self.precision = precision
+        if precision == "fp64":
+            self.apply_A = A.apply
+            self.dinv = 1.0 / A.diagonal()
+            self.dt = np.float64
+        else:
+            rs = RoundedStencil(A, precision)
+            self.apply_A = rs.apply
+            self.dinv = rs.dinv.reshape(-1)
+            self.dt = np.float32
+
+    def __call__(self, v):
+        dt = self.dt
+        v = np.asarray(v, dtype=np.float64).astype(dt)
+        x = np.zeros_like(v)
+        r = v.copy()                      # r_0 = v - A x_0, x_0 = 0
+        u = (self.dinv * r).astype(dt)    # u_0 = M^-1 r_0
+        p = u.copy()                      # p_0 = u_0
+        s = self.apply_A(p).astype(dt)    # s_0 = A p_0
+        gamma = _dot(u, r)
+        eta = _dot(s, p)
+        if gamma == 0.0 or eta == 0.0:
+            return x.astype(np.float64)
+        alpha = gamma / eta
+        for i in range(1, self.k + 1):
+            x = (x + dt(alpha) * p).astype(dt)
+            if i == self.k:
+                break
+            r = (r - dt(alpha) * s).astype(dt)
+            u = (self.dinv * r).astype(dt)
+            gamma_new = _dot(u, r)
+            if gamma_new == 0.0:
+                break
+            beta = gamma_new / gamma
+            gamma = gamma_new
+            p = (u + dt(beta) * p).astype(dt)
+            s = self.apply_A(p).astype(dt)
+            eta = _dot(s, p)
+            if eta == 0.0:
+                break
+            alpha = gamma / eta
+        return x.astype(np.float64)
+
+
+def chebyshev_bounds(A) -> tuple:
+    """[0.1 lam, 1.1 lam] with lam the Gershgorin bound max_i sum_j |a_ij| / a_ii."""
+    lam = A.gershgorin_jacobi_bound()
+    return 0.1 * lam, 1.1 * lam
+
+
+class Chebyshev:
+    """k Chebyshev sweeps for D^-1 A x = D^-1 v from x_0 = 0 over [lo, hi].
+
+    theta = (hi + lo)/2, delta = (hi - lo)/2, sigma_1 = theta/delta,
+    rho_0 = 1/sigma_1, r_0 = v, d_0 = D^-1 r_0 / theta; for j = 0..k-1:
+    x_{j+1} = x_j + d_j; if j+1 < k: r_{j+1} = r_j - A d_j,
+    rho_{j+1} = 1/(2 sigma_1 - rho_j),
+    d_{j+1} = rho_{j+1} rho_j d_j + (2 rho_{j+1}/delta) D^-1 r_{j+1}.
+    Returns x_k (k - 1 operator applications).
+    """
+
+    linear = True
+
+    def __init__(self, A, k: int, lo: float = None, hi: float = None, precision: str = "fp64"):
+        if lo is None or hi is None:
+            lo, hi = chebyshev_bounds(A)
+        self.lo, self.hi = float(lo), float(hi)
+        self.k = int(k)
+        self.precision = precision
+        if precision == "fp64":
+            self.apply_A = A.apply
+            self.dinv = 1.0 / A.diagonal()
+            self.dt = np.float64
+        else:
+            rs = RoundedStencil(A, precision)
+            self.apply_A = rs.apply
+            self.dinv = rs.dinv.reshape(-1)
+            self.dt = np.float32
+
+    def __call__(self, v):
+        dt = self.dt
+        theta = (self.hi + self.lo) / 2.0
+        delta = (self.hi - self.lo) / 2.0
+        sigma1 = theta / delta
+        rho = 1.0 / sigma1
+        r = np.asarray(v, dtype=np.float64).astype(dt)
+        x = np.zeros_like(r)
+        d = (self.dinv * r / dt(theta)).astype(dt)
+        for j in range(self.k):
+            x = (x + d).astype(dt)
+            if j + 1 == self.k:
+                break
+            r = (r - self.apply_A(d)).astype(dt)
+            rho_new = 1.0 / (2.0 * sigma1 - rho)
+            d = (dt(rho_new * rho) * d + dt(2.0 * rho_new / delta) * (self.dinv * r)).astype(dt)
+            rho = rho_new
+        return x.astype(np.float64)
