@@ -1,0 +1,293 @@
+/*
+ * pfk.h -- C ABI of the GB300 pipelined flexible Krylov library.
+ *
+ * The library solves A x = b with the flexible Krylov methods of Sanan,
+ * Schnepp and May, "Pipelined, Flexible Krylov Subspace Methods"
+ * (arXiv 1511.07226): the problem statement is the one of Alg. 2 (FCG(A, B,
+ * b, x0)) and Alg. 13 (FGMRES(A, B, b, x0, m)): an operator A, a possibly
+ * nonlinear preconditioner B, a right-hand side b, an initial guess x0, a
+ * relative tolerance and the truncation length nu_max (CG/CR types) or the
+ * restart length m (GMRES types), Sec. 5 "Implementation".
+ *
+ * Every step of a solve runs in the library's CUDA kernels for sm_103a on one
+ * GPU; there is no CPU fallback.  A call that needs the GPU and cannot get it
+ * returns PFK_ERR_CUDA.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns a pfk_status; no C++ exception crosses the ABI.
+ *  - Handles are opaque, created by pfk_create_* and owned by the library
+ *    until the matching pfk_destroy_*; destroying NULL is a no-op.
+ *  - Array arguments are borrowed for the duration of the call only; the
+ *    library copies what it keeps.
+ *  - "device pointer" means memory of the context's GPU (cudaMalloc, the
+ *    PyTorch caching allocator, ...); "host pointer" means ordinary host
+ *    memory.  Functions that take both say which via an explicit flag.
+ *  - All device work is ordered on the context's CUDA stream.  Calls return
+ *    after that work is complete unless stated otherwise.
+ *  - A context is used by one host thread at a time.  pfk_last_error() holds
+ *    the message of the last failing call on that context (or, for a NULL
+ *    context, on the calling thread).
+ *  - Vectors are FP64, length n, in the cell order index = i + nx (j + ny k).
+ */
+#ifndef PFK_H_
+#define PFK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFK_ABI_VERSION 1
+#define PFK_MAX_MMAX 32        /* largest nu_max / restart length m */
+#define PFK_HISTORY_FIELDS 4   /* per iteration: rho, ||r||_2 (recurred), eta, alpha */
+
+typedef enum {
+  PFK_OK = 0,
+  PFK_PENDING = 1,
+  PFK_ERR_INVALID = -1,       /* bad argument; nothing was done */
+  PFK_ERR_OOM = -2,           /* device allocation failed */
+  PFK_ERR_CUDA = -3,          /* a CUDA call failed; the message has the CUDA error */
+  PFK_ERR_BREAKDOWN = -4,     /* norm breakdown that restarting could not cure (Sec. 5) */
+  PFK_ERR_NOT_CONVERGED = -5, /* maxit reached; x holds the last iterate */
+  PFK_ERR_TIMEOUT = -6,       /* a bounded device or host wait gave up */
+  PFK_ERR_CANCELLED = -7,
+  PFK_ERR_BUSY = -8           /* server queue full */
+} pfk_status;
+
+typedef enum {
+  PFK_STENCIL5_2D = 0,  /* -div(eta grad u) on nx x ny cells (nz = 1) */
+  PFK_STENCIL7_3D = 1,  /* -div(eta grad u) on nx x ny x nz cells */
+  PFK_CSR = 2           /* general sparse matrix in CSR form */
+} pfk_op_kind;
+
+typedef enum {
+  PFK_STORAGE_MATRIX_FREE = 0, /* stencils: face coefficients + diagonal, applied on the fly */
+  PFK_STORAGE_CSR = 1          /* stencils: assembled by the library into FP64 CSR */
+} pfk_op_storage;
+
+typedef enum {
+  PFK_FCG = 0,          /* Alg. 2 */
+  PFK_PIPEFCG = 1,      /* Alg. 8 */
+  PFK_GCR = 2,          /* Alg. 9 */
+  PFK_PIPEGCR = 3,      /* Alg. 11 */
+  PFK_FGMRES = 4,       /* Alg. 13 */
+  PFK_PIPEFGMRES = 5,   /* Alg. 15 */
+  PFK_PIPEFCG_NAIVE = 6 /* Alg. 7 */
+} pfk_method;
+
+typedef enum {
+  PFK_PC_NONE = 0,       /* B(v) = v */
+  PFK_PC_JACOBI = 1,     /* B(v) = D^-1 v */
+  PFK_PC_INNER_PCG = 2,  /* inner_iters iterations of Jacobi-PCG (Alg. 3, M^-1 = D^-1) from 0 */
+  PFK_PC_CHEBYSHEV = 3   /* inner_iters Chebyshev-Jacobi sweeps from 0 */
+} pfk_pc_kind;
+
+typedef enum {
+  PFK_FP64 = 0,          /* preconditioner arithmetic and storage in FP64 */
+  PFK_FP32 = 1,          /* FP32 vectors and coefficient copies, FP64 dot combination */
+  PFK_BF16_COEF_FP32 = 2 /* BF16-stored coefficients, FP32 vectors and accumulation */
+} pfk_precision;
+
+typedef enum { PFK_TRUNC_STANDARD = 0, PFK_TRUNC_RESTART = 1 } pfk_truncation;
+typedef enum { PFK_NORM_NATURAL = 0, PFK_NORM_UNPRECONDITIONED = 1 } pfk_norm;
+
+typedef struct pfk_context pfk_context;
+typedef struct pfk_operator pfk_operator;
+typedef struct pfk_pc pfk_pc;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` whose work is ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * stream stays owned by the caller and must outlive the context.
+ * Errors: PFK_ERR_INVALID (ctx NULL or bad device), PFK_ERR_CUDA. */
+pfk_status pfk_create_context(int device, void* cuda_stream, pfk_context** ctx);
+pfk_status pfk_destroy_context(pfk_context* ctx);
+
+/* Message of the last failing call on ctx (ctx may be NULL: calling thread). */
+const char* pfk_last_error(const pfk_context* ctx);
+
+/* ABI version (PFK_ABI_VERSION) of the loaded library. */
+int pfk_abi_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Operators                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Stencil kinds: cell-centred finite volumes for -div(eta grad u) on the unit
+ * square/cube with homogeneous Dirichlet boundaries, scaled so that
+ *   (A u)_i = sum over faces f of cell i of K_f (u_i - u_nbr),
+ *   K_f = 2 eta_i eta_j / (eta_i + eta_j) on interior faces, 2 eta_i with
+ *   u_nbr = 0 on boundary faces,
+ * plus, if vel != 0, first-order upwind advection h |v_d| (u_i - u_up) per
+ * direction (h = 1/nx; upwind ghost outside the domain = 0).  This is the
+ * n_z = 7 (3D) sparse operator of the paper's performance model (Sec. 8).
+ * The right-hand side the caller passes is then h^2 f.
+ *
+ * CSR kind: n rows, nnz entries, int32 row pointers (n+1) and column indices,
+ * FP64 values; columns need not be sorted.
+ *
+ * Ownership: eta / rowptr / colidx / vals are read during the call only; their
+ * location is given by eta_on_device / csr_on_device (0 = host, 1 = device).
+ * Errors: PFK_ERR_INVALID (sizes <= 0, nz != 1 for 2D, eta <= 0 is not checked
+ * on device data), PFK_ERR_OOM, PFK_ERR_CUDA. */
+typedef struct {
+  int32_t kind;        /* pfk_op_kind */
+  int32_t storage;     /* pfk_op_storage (stencils only) */
+  int32_t nx, ny, nz;  /* stencils */
+  const double* eta;   /* stencils: nx*ny*nz cell viscosities, > 0 */
+  int32_t eta_on_device;
+  double vel[3];       /* stencils: constant advection velocity (0 = none) */
+  int64_t n, nnz;      /* CSR */
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const double* vals;
+  int32_t csr_on_device;
+} pfk_operator_desc;
+
+pfk_status pfk_create_operator(pfk_context* ctx, const pfk_operator_desc* desc, pfk_operator** op);
+pfk_status pfk_destroy_operator(pfk_operator* op);
+/* Number of rows n of the operator. */
+pfk_status pfk_operator_size(const pfk_operator* op, int64_t* n);
+/* y = A x; x and y are device pointers of length n, must not overlap. */
+pfk_status pfk_operator_apply(pfk_context* ctx, const pfk_operator* op, const double* x, double* y);
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioners                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* The preconditioner B of the flexible methods (Sec. 2): any map v -> B(v);
+ * the inner iterative ones are nonlinear in v.
+ *  - JACOBI: B(v) = D^-1 v, D = diag(A).
+ *  - INNER_PCG: `inner_iters` iterations of Alg. 3 with M^-1 = D^-1 on A y = v
+ *    from y = 0, no tolerance test; the experiments of Sec. 6 use 5 such
+ *    iterations per block.  If <D^-1 r, r> or <s, p> becomes exactly 0 the
+ *    current iterate is returned.
+ *  - CHEBYSHEV: `inner_iters` Chebyshev sweeps on D^-1 A over [cheb_lo,
+ *    cheb_hi] from 0 (Saad, Iterative Methods for Sparse Linear Systems, 2nd
+ *    ed., Alg. 12.1).  cheb_lo = cheb_hi = 0 selects [0.1 L, 1.1 L] with L the
+ *    Gershgorin bound max_i sum_j |a_ij| / a_ii.
+ *  - precision: PFK_FP64, PFK_FP32 (INNER_PCG, CHEBYSHEV) or
+ *    PFK_BF16_COEF_FP32 (CHEBYSHEV): the preconditioner's copy of A stores the
+ *    diagonal, the face coefficients and D^-1 rounded FP64 -> FP32 (-> BF16,
+ *    nearest-even); its vectors are FP32; the outer method stays FP64.
+ * Stencil operators support every kind; CSR operators support NONE and JACOBI.
+ * The preconditioner keeps a reference to `op`, which must outlive it. */
+typedef struct {
+  int32_t kind;        /* pfk_pc_kind */
+  int32_t inner_iters;
+  int32_t precision;   /* pfk_precision */
+  double cheb_lo, cheb_hi;
+} pfk_pc_desc;
+
+pfk_status pfk_create_preconditioner(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc* desc,
+                                     pfk_pc** pc);
+pfk_status pfk_destroy_preconditioner(pfk_pc* pc);
+/* y = B(v); device pointers of length n, must not overlap. */
+pfk_status pfk_pc_apply(pfk_context* ctx, const pfk_pc* pc, const double* v, double* y);
+
+/* ------------------------------------------------------------------------ */
+/* Solve                                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Solve parameters.
+ *  method      pfk_method.
+ *  mmax        nu_max (FCG/PIPEFCG/GCR/PIPEGCR) or restart length m
+ *              (FGMRES/PIPEFGMRES); 1 <= mmax <= PFK_MAX_MMAX.
+ *  truncation  STANDARD: nu_i = min(i, nu_max); RESTART: nu_i =
+ *              ((i-1) mod nu_max) + 1, i counted since the last (re)start
+ *              ("Truncation strategies", Sec. 5).
+ *  norm        NATURAL: sqrt|gamma_i| (CG/CR types; the only norm free of
+ *              extra reductions, Sec. 5); UNPRECONDITIONED: recurred ||r_i||_2.
+ *              GMRES types always use the least-squares residual estimate.
+ *  rtol, atol  converged when rho_i <= max(rtol rho_0, atol), rho_0 from the
+ *              first pipeline fill.
+ *  maxit       iteration limit (all restarts together).
+ *  max_restarts  bound on breakdown restarts plus residual replacements.
+ *  sigma       constant shift of PIPEFGMRES (Sec. 5.3); NaN = estimate it by
+ *              10 power iterations on v -> A B(v).
+ *  true_residual_check  1: at convergence require ||b - A x||_2 <= rtol ||b||_2
+ *              (else restart from x with the target tightened by
+ *              0.5 rtol ||b|| / ||b - A x||); 0: accept the recurred norm.
+ *  graph_iters iterations per captured CUDA graph launch (0 = default 8).
+ *  history     optional HOST buffer of history_capacity * PFK_HISTORY_FIELDS
+ *              doubles; entry e = (rho, ||r||_2 recurred or NaN, eta, alpha)
+ *              for each pipeline fill and each iteration, in order.
+ *  profile     1: record CUDA events around the method's fused recurrence
+ *              pass in every iteration (the graphs then carry event nodes and
+ *              one graph launch is in flight instead of two) and report the
+ *              pass's total device time in pfk_solve_info.pass_ms. */
+typedef struct {
+  int32_t method;
+  int32_t mmax;
+  int32_t truncation;
+  int32_t norm;
+  double rtol;
+  double atol;
+  int32_t maxit;
+  int32_t max_restarts;
+  double sigma;
+  int32_t true_residual_check;
+  int32_t graph_iters;
+  double* history;
+  int32_t history_capacity;
+  int32_t profile;
+} pfk_solve_params;
+
+typedef struct {
+  int32_t status;       /* pfk_status of the solve */
+  int32_t iterations;
+  int32_t restarts;     /* breakdown restarts + residual replacements */
+  int32_t breakdowns;
+  int32_t replacements;
+  int32_t history_len;  /* entries written (may exceed capacity: then truncated) */
+  double rho0, rho_final;
+  double rnorm_true;    /* ||b - A x||_2 at exit */
+  double bnorm;         /* ||b||_2 */
+  double time_ms;       /* device time of the solve, CUDA events on the stream */
+  /* Accounting of the fused recurrence pass (the dominant kernel), over the
+   * passes that did work: launches, algorithmic HBM bytes (each vector read or
+   * written once per pass) and FP64 flops (FMA = 2), and, with profile = 1,
+   * the summed device time of those passes. */
+  int32_t pass_launches;
+  int32_t kernel_launches;  /* all library kernels launched by the solve */
+  double pass_bytes;
+  double pass_flops;
+  double pass_ms;
+} pfk_solve_info;
+
+/* Fills `params` with the defaults: PIPEFCG, mmax 30, standard truncation,
+ * natural norm, rtol 1e-8, atol 0, maxit 10000, max_restarts 20, sigma NaN,
+ * true_residual_check 1, graph_iters 8, no history. */
+pfk_status pfk_default_params(pfk_solve_params* params);
+
+/* Solves A x = b.  b and x are host pointers (ptr_on_device = 0) or device
+ * pointers (1), length n; x holds x0 on entry and the solution on exit (also
+ * on PFK_ERR_NOT_CONVERGED and PFK_ERR_BREAKDOWN, where it is the last
+ * iterate).  `pc` may be NULL (= PFK_PC_NONE).  info may be NULL.
+ * Returns PFK_OK on convergence, PFK_ERR_NOT_CONVERGED at maxit,
+ * PFK_ERR_BREAKDOWN (Sec. 5: breakdown in a fill or right after a breakdown
+ * restart, or restarts exhausted), PFK_ERR_INVALID, PFK_ERR_OOM, PFK_ERR_CUDA. */
+pfk_status pfk_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, const pfk_solve_params* params,
+                     const double* b, double* x, int ptr_on_device, pfk_solve_info* info);
+
+/* Number of length-n vectors the paper counts for a method's storage:
+ * PIPEFCG 4 nu+11, FCG nu+6 (Sec. 3.2.3); GCR 2 nu+7, PIPEGCR 3 nu+9 (Sec. 4);
+ * FGMRES 2m+2, PIPEFGMRES 4m+2 (Sec. 5.3).  Returns -1 for a bad method. */
+int pfk_method_storage_vectors(int method, int mmax);
+
+/* Device bytes pfk_solve allocates for one solve of size n (vectors, rings,
+ * partial sums, control block; excludes the preconditioner's own scratch,
+ * reported by pfk_pc_workspace_bytes). */
+pfk_status pfk_solve_workspace_bytes(int method, int mmax, int64_t n, int64_t* bytes);
+pfk_status pfk_pc_workspace_bytes(const pfk_pc* pc, int64_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFK_H_ */

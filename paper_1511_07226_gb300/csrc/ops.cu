@@ -1,0 +1,402 @@
+// Operators: setup of the finite-volume stencil coefficients, matrix-free
+// stencil application (FP64 and the reduced-precision copies used inside
+// preconditioners), CSR assembly and CSR SpMV, and the dot-product kernel.
+//
+// The operator is the n_z = 7 (3D) / 5 (2D) sparse matrix of the paper's
+// performance model (Sec. 8): the T_spmv term of every method.  It is the
+// "A" of every listing (Algs. 2-15).
+#include "pfk_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace pfk {
+
+// ---------------------------------------------------------------------------
+// Coefficient setup
+// ---------------------------------------------------------------------------
+
+// Harmonic mean of two cell viscosities, 2 a b / (a + b), rounded operation by
+// operation (no contraction) so both orientations of a face agree bitwise.
+__device__ __forceinline__ double harmonic(double a, double b) {
+  return __ddiv_rn(__dmul_rn(__dmul_rn(2.0, a), b), __dadd_rn(a, b));
+}
+
+__global__ void stencil_setup_kernel(const double* __restrict__ eta, int nx, int ny, int nz, int ndim,
+                                     double a0, double a1, double a2, double* __restrict__ d,
+                                     double* __restrict__ kx, double* __restrict__ ky, double* __restrict__ kz,
+                                     double* __restrict__ dinv, int64_t n) {
+  const int64_t sxy = (int64_t)nx * ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / sxy);
+    const double e = eta[c];
+    const double twoe = __dmul_rn(2.0, e);
+    const double fxm = (i > 0) ? harmonic(e, eta[c - 1]) : twoe;
+    const double fxp = (i < nx - 1) ? harmonic(e, eta[c + 1]) : twoe;
+    const double fym = (j > 0) ? harmonic(e, eta[c - nx]) : twoe;
+    const double fyp = (j < ny - 1) ? harmonic(e, eta[c + nx]) : twoe;
+    double dg = __dadd_rn(__dadd_rn(__dadd_rn(fxm, fxp), fym), fyp);
+    double fzp = 0.0;
+    if (ndim == 3) {
+      const double fzm = (k > 0) ? harmonic(e, eta[c - sxy]) : twoe;
+      fzp = (k < nz - 1) ? harmonic(e, eta[c + sxy]) : twoe;
+      dg = __dadd_rn(__dadd_rn(dg, fzm), fzp);
+    }
+    dg = __dadd_rn(__dadd_rn(dg, a0), a1);
+    if (ndim == 3) dg = __dadd_rn(dg, a2);
+    d[c] = dg;
+    kx[c] = (i < nx - 1) ? fxp : 0.0;
+    ky[c] = (j < ny - 1) ? fyp : 0.0;
+    if (ndim == 3) kz[c] = (k < nz - 1) ? fzp : 0.0;
+    dinv[c] = __ddiv_rn(1.0, dg);
+  }
+}
+
+// Row-wise Gershgorin ratio sum_j |a_ij| / a_ii of the stencil (for Chebyshev
+// bounds); max over rows by a last-block reduction of per-block maxima.
+__global__ void gershgorin_kernel(const double* __restrict__ d, const double* __restrict__ kx,
+                                  const double* __restrict__ ky, const double* __restrict__ kz, int nx, int ny,
+                                  int nz, int ndim, double a0, double a1, double a2, int u0, int u1, int u2,
+                                  int64_t n, double* partials, unsigned int* counter, double* out) {
+  const int64_t sxy = (int64_t)nx * ny;
+  double m = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / sxy);
+    double s = d[c];
+    // off-diagonals: -K on interior faces, plus -a at the interior upwind neighbour
+    if (i < nx - 1) s += kx[c] + (u0 == 1 ? a0 : 0.0);
+    if (i > 0) s += kx[c - 1] + (u0 == -1 ? a0 : 0.0);
+    if (j < ny - 1) s += ky[c] + (u1 == 1 ? a1 : 0.0);
+    if (j > 0) s += ky[c - nx] + (u1 == -1 ? a1 : 0.0);
+    if (ndim == 3) {
+      if (k < nz - 1) s += kz[c] + (u2 == 1 ? a2 : 0.0);
+      if (k > 0) s += kz[c - sxy] + (u2 == -1 ? a2 : 0.0);
+    }
+    m = fmax(m, s / d[c]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[kThreads / 32];
+  __shared__ unsigned int last;
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, sm[w]);
+    partials[blockIdx.x] = v;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double v = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) v = fmax(v, __ldcg(&partials[b]));
+    *out = v;
+    *counter = 0u;
+  }
+}
+
+template <typename T>
+__global__ void round_copy_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n);
+
+template <>
+__global__ void round_copy_kernel<float>(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    dst[c] = __double2float_rn(src[c]);
+}
+
+template <>
+__global__ void round_copy_kernel<__nv_bfloat16>(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                 int64_t n) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    dst[c] = __float2bfloat16_rn(__double2float_rn(src[c]));
+}
+
+// ---------------------------------------------------------------------------
+// Matrix-free stencil application
+// ---------------------------------------------------------------------------
+
+template <typename C>
+__device__ __forceinline__ float coef(C v);
+template <>
+__device__ __forceinline__ float coef<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float coef<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// y = A m (or y = b - A m) in FP64:
+//   (A m)_c = d_c m_c - sum_faces K_f m_nbr - a_d m_up
+struct StencilArgs {
+  const double* d;
+  const double* kx;
+  const double* ky;
+  const double* kz;
+  int nx, ny, nz, ndim;
+  double a0, a1, a2;
+  int u0, u1, u2;
+  int64_t n;
+};
+
+__device__ __forceinline__ double stencil_row(const StencilArgs& A, const double* __restrict__ m, int64_t c) {
+  const int64_t sxy = (int64_t)A.nx * A.ny;
+  const int i = (int)(c % A.nx);
+  const int j = (int)((c / A.nx) % A.ny);
+  double acc = A.d[c] * m[c];
+  if (i > 0) acc = fma(-(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)), m[c - 1], acc);
+  if (i < A.nx - 1) acc = fma(-(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)), m[c + 1], acc);
+  if (j > 0) acc = fma(-(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)), m[c - A.nx], acc);
+  if (j < A.ny - 1) acc = fma(-(A.ky[c] + (A.u1 == 1 ? A.a1 : 0.0)), m[c + A.nx], acc);
+  if (A.ndim == 3) {
+    const int k = (int)(c / sxy);
+    if (k > 0) acc = fma(-(A.kz[c - sxy] + (A.u2 == -1 ? A.a2 : 0.0)), m[c - sxy], acc);
+    if (k < A.nz - 1) acc = fma(-(A.kz[c] + (A.u2 == 1 ? A.a2 : 0.0)), m[c + sxy], acc);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kThreads) stencil_apply_kernel(StencilArgs A, const double* __restrict__ m,
+                                                                 double* __restrict__ y,
+                                                                 const double* __restrict__ bsub,
+                                                                 const int* __restrict__ status) {
+  if (status && *status != kRun) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < A.n; c += (int64_t)gridDim.x * blockDim.x) {
+    double v = stencil_row(A, m, c);
+    y[c] = bsub ? bsub[c] - v : v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CSR
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) csr_apply_kernel(const int32_t* __restrict__ rowptr,
+                                                             const int32_t* __restrict__ colidx,
+                                                             const double* __restrict__ vals,
+                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             const double* __restrict__ bsub, int64_t n,
+                                                             const int* __restrict__ status) {
+  if (status && *status != kRun) return;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    const int32_t e = rowptr[r + 1];
+    for (int32_t p = rowptr[r]; p < e; ++p) acc = fma(vals[p], x[colidx[p]], acc);
+    y[r] = bsub ? bsub[r] - acc : acc;
+  }
+}
+
+// Assembles the stencil as CSR; neighbours in ascending column order
+// (-z, -y, -x, diagonal, +x, +y, +z); rowptr is precomputed on the host from
+// the geometry alone.
+__global__ void stencil_to_csr_kernel(StencilArgs A, const int32_t* __restrict__ rowptr,
+                                      int32_t* __restrict__ colidx, double* __restrict__ vals) {
+  const int64_t sxy = (int64_t)A.nx * A.ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < A.n; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % A.nx);
+    const int j = (int)((c / A.nx) % A.ny);
+    const int k = (int)(c / sxy);
+    int32_t p = rowptr[c];
+    if (A.ndim == 3 && k > 0) { colidx[p] = (int32_t)(c - sxy); vals[p++] = -(A.kz[c - sxy] + (A.u2 == -1 ? A.a2 : 0.0)); }
+    if (j > 0) { colidx[p] = (int32_t)(c - A.nx); vals[p++] = -(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)); }
+    if (i > 0) { colidx[p] = (int32_t)(c - 1); vals[p++] = -(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)); }
+    colidx[p] = (int32_t)c;
+    vals[p++] = A.d[c];
+    if (i < A.nx - 1) { colidx[p] = (int32_t)(c + 1); vals[p++] = -(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)); }
+    if (j < A.ny - 1) { colidx[p] = (int32_t)(c + A.nx); vals[p++] = -(A.ky[c] + (A.u1 == 1 ? A.a1 : 0.0)); }
+    if (A.ndim == 3 && k < A.nz - 1) { colidx[p] = (int32_t)(c + sxy); vals[p++] = -(A.kz[c] + (A.u2 == 1 ? A.a2 : 0.0)); }
+  }
+}
+
+__global__ void csr_diag_inv_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                    const double* __restrict__ vals, double* __restrict__ dinv, int64_t n,
+                                    int* bad) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double dg = 0.0;
+    for (int32_t p = rowptr[r]; p < rowptr[r + 1]; ++p)
+      if (colidx[p] == r) dg += vals[p];
+    if (dg == 0.0) atomicExch(bad, 1);
+    dinv[r] = dg != 0.0 ? __ddiv_rn(1.0, dg) : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dot product
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) dot_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                       int64_t n, double* partials, unsigned int* counter,
+                                                       double* out) {
+  double acc[1] = {0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    acc[0] = fma(a[c], b[c], acc[0]);
+  __shared__ double smem[kThreads / 32];
+  __shared__ double sums[1];
+  if (reduce_last_block<1>(acc, 1, partials, 1, counter, smem, sums)) {
+    if (threadIdx.x == 0) *out = sums[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+int stream_blocks(const pfk_context* ctx, int64_t n, int blocks_per_sm) {
+  int64_t need = (n + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)ctx->num_sms * blocks_per_sm;
+  int64_t b = need < cap ? need : cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+static StencilArgs stencil_args(const pfk_operator* op) {
+  StencilArgs A;
+  A.d = op->d; A.kx = op->kx; A.ky = op->ky; A.kz = op->kz;
+  A.nx = op->nx; A.ny = op->ny; A.nz = op->nz; A.ndim = op->ndim;
+  A.a0 = op->adv[0]; A.a1 = op->adv[1]; A.a2 = op->adv[2];
+  A.u0 = op->upw[0]; A.u1 = op->upw[1]; A.u2 = op->upw[2];
+  A.n = op->n;
+  return A;
+}
+
+cudaError_t op_apply(const pfk_operator* op, const double* x, double* y, const double* bsub, const int* status,
+                     cudaStream_t st) {
+  const int blocks = stream_blocks(op->ctx, op->n, 8);
+  if (op->rowptr) {
+    csr_apply_kernel<<<blocks, kThreads, 0, st>>>(op->rowptr, op->colidx, op->vals, x, y, bsub, op->n, status);
+  } else {
+    stencil_apply_kernel<<<blocks, kThreads, 0, st>>>(stencil_args(op), x, y, bsub, status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t dot_into(pfk_context* ctx, const double* a, const double* b, int64_t n, double* out, cudaStream_t st) {
+  const int blocks = stream_blocks(ctx, n, 2);
+  dot_kernel<<<blocks, kThreads, 0, st>>>(a, b, n, ctx->scratch_partials, ctx->scratch_counter, out);
+  return cudaGetLastError();
+}
+
+// Reduced-precision copies of the stencil for the mixed-precision preconditioners.
+pfk_status ensure_reduced_copies(pfk_operator* op, int precision) {
+  pfk_context* ctx = op->ctx;
+  const int64_t n = op->n;
+  const int blocks = stream_blocks(ctx, n, 8);
+  if (precision == PFK_FP32 && !op->d32) {
+    float** dst[5] = {&op->d32, &op->kx32, &op->ky32, &op->kz32, &op->dinv32};
+    const double* src[5] = {op->d, op->kx, op->ky, op->kz, op->dinv};
+    for (int t = 0; t < 5; ++t) {
+      if (t == 3 && op->ndim != 3) continue;
+      PFK_CUDA(ctx, cudaMallocAsync((void**)dst[t], n * sizeof(float), ctx->stream));
+      round_copy_kernel<float><<<blocks, kThreads, 0, ctx->stream>>>(src[t], *dst[t], n);
+      PFK_CUDA(ctx, cudaGetLastError());
+    }
+  }
+  if (precision == PFK_BF16_COEF_FP32 && !op->d16) {
+    __nv_bfloat16** dst[5] = {&op->d16, &op->kx16, &op->ky16, &op->kz16, &op->dinv16};
+    const double* src[5] = {op->d, op->kx, op->ky, op->kz, op->dinv};
+    for (int t = 0; t < 5; ++t) {
+      if (t == 3 && op->ndim != 3) continue;
+      PFK_CUDA(ctx, cudaMallocAsync((void**)dst[t], n * sizeof(__nv_bfloat16), ctx->stream));
+      round_copy_kernel<__nv_bfloat16><<<blocks, kThreads, 0, ctx->stream>>>(src[t], *dst[t], n);
+      PFK_CUDA(ctx, cudaGetLastError());
+    }
+  }
+  return PFK_OK;
+}
+
+pfk_status create_stencil(pfk_context* ctx, const pfk_operator_desc* desc, pfk_operator* op) {
+  op->nx = desc->nx; op->ny = desc->ny; op->nz = desc->kind == PFK_STENCIL5_2D ? 1 : desc->nz;
+  op->ndim = desc->kind == PFK_STENCIL5_2D ? 2 : 3;
+  op->n = (int64_t)op->nx * op->ny * op->nz;
+  const int64_t n = op->n;
+  const double h = 1.0 / op->nx;
+  for (int dd = 0; dd < 3; ++dd) {
+    const double v = desc->vel[dd];
+    if (dd >= op->ndim || v == 0.0) { op->adv[dd] = 0.0; op->upw[dd] = 0; continue; }
+    op->adv[dd] = h * std::fabs(v);
+    op->upw[dd] = v > 0 ? -1 : 1;
+  }
+  cudaStream_t st = ctx->stream;
+  double** arrs[5] = {&op->d, &op->kx, &op->ky, &op->kz, &op->dinv};
+  for (int t = 0; t < 5; ++t) {
+    if (t == 3 && op->ndim != 3) continue;
+    cudaError_t e = cudaMallocAsync((void**)arrs[t], n * sizeof(double), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (set_error(ctx, "out of device memory"), PFK_ERR_OOM)
+                                                                : cuda_fail(ctx, e, "cudaMallocAsync");
+  }
+  const double* eta = desc->eta;
+  double* eta_dev = nullptr;
+  if (!desc->eta_on_device) {
+    PFK_CUDA(ctx, cudaMallocAsync((void**)&eta_dev, n * sizeof(double), st));
+    PFK_CUDA(ctx, cudaMemcpyAsync(eta_dev, desc->eta, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    eta = eta_dev;
+  }
+  const int blocks = stream_blocks(ctx, n, 8);
+  stencil_setup_kernel<<<blocks, kThreads, 0, st>>>(eta, op->nx, op->ny, op->nz, op->ndim, op->adv[0], op->adv[1],
+                                                    op->adv[2], op->d, op->kx, op->ky, op->ndim == 3 ? op->kz : nullptr,
+                                                    op->dinv, n);
+  PFK_CUDA(ctx, cudaGetLastError());
+  // Gershgorin bound
+  {
+    double* out = ctx->scratch_out;
+    const int gb = stream_blocks(ctx, n, 2);
+    gershgorin_kernel<<<gb, kThreads, 0, st>>>(op->d, op->kx, op->ky, op->kz, op->nx, op->ny, op->nz, op->ndim,
+                                               op->adv[0], op->adv[1], op->adv[2], op->upw[0], op->upw[1], op->upw[2],
+                                               n, ctx->scratch_partials, ctx->scratch_counter, out);
+    PFK_CUDA(ctx, cudaGetLastError());
+    PFK_CUDA(ctx, cudaMemcpyAsync(&op->gersh, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  if (eta_dev) PFK_CUDA(ctx, cudaFreeAsync(eta_dev, st));
+  if (desc->storage == PFK_STORAGE_CSR) {
+    if (n > INT32_MAX / 8) { set_error(ctx, "stencil too large for int32 CSR"); return PFK_ERR_INVALID; }
+    std::vector<int32_t> rp(n + 1);
+    rp[0] = 0;
+    const int64_t sxy = (int64_t)op->nx * op->ny;
+    for (int64_t c = 0; c < n; ++c) {
+      const int i = (int)(c % op->nx), j = (int)((c / op->nx) % op->ny), k = (int)(c / sxy);
+      int cnt = 1 + (i > 0) + (i < op->nx - 1) + (j > 0) + (j < op->ny - 1);
+      if (op->ndim == 3) cnt += (k > 0) + (k < op->nz - 1);
+      rp[c + 1] = rp[c] + cnt;
+    }
+    op->nnz = rp[n];
+    PFK_CUDA(ctx, cudaMallocAsync((void**)&op->rowptr, (n + 1) * sizeof(int32_t), st));
+    PFK_CUDA(ctx, cudaMallocAsync((void**)&op->colidx, op->nnz * sizeof(int32_t), st));
+    PFK_CUDA(ctx, cudaMallocAsync((void**)&op->vals, op->nnz * sizeof(double), st));
+    PFK_CUDA(ctx, cudaMemcpyAsync(op->rowptr, rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    stencil_to_csr_kernel<<<blocks, kThreads, 0, st>>>(stencil_args(op), op->rowptr, op->colidx, op->vals);
+    PFK_CUDA(ctx, cudaGetLastError());
+    PFK_CUDA(ctx, cudaStreamSynchronize(st));   // rp is a host temporary
+  }
+  PFK_CUDA(ctx, cudaStreamSynchronize(st));
+  return PFK_OK;
+}
+
+pfk_status create_csr(pfk_context* ctx, const pfk_operator_desc* desc, pfk_operator* op) {
+  const int64_t n = desc->n, nnz = desc->nnz;
+  op->n = n;
+  op->nnz = nnz;
+  cudaStream_t st = ctx->stream;
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&op->rowptr, (n + 1) * sizeof(int32_t), st));
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&op->colidx, (nnz > 0 ? nnz : 1) * sizeof(int32_t), st));
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&op->vals, (nnz > 0 ? nnz : 1) * sizeof(double), st));
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&op->csr_dinv, n * sizeof(double), st));
+  const cudaMemcpyKind kind = desc->csr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  PFK_CUDA(ctx, cudaMemcpyAsync(op->rowptr, desc->rowptr, (n + 1) * sizeof(int32_t), kind, st));
+  if (nnz > 0) {
+    PFK_CUDA(ctx, cudaMemcpyAsync(op->colidx, desc->colidx, nnz * sizeof(int32_t), kind, st));
+    PFK_CUDA(ctx, cudaMemcpyAsync(op->vals, desc->vals, nnz * sizeof(double), kind, st));
+  }
+  int* bad = (int*)ctx->scratch_counter + 1;
+  PFK_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), st));
+  csr_diag_inv_kernel<<<stream_blocks(ctx, n, 8), kThreads, 0, st>>>(op->rowptr, op->colidx, op->vals, op->csr_dinv,
+                                                                     n, bad);
+  PFK_CUDA(ctx, cudaGetLastError());
+  int hbad = 0;
+  PFK_CUDA(ctx, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PFK_CUDA(ctx, cudaStreamSynchronize(st));
+  (void)hbad;   // a zero diagonal only matters for the Jacobi preconditioner (checked there)
+  return PFK_OK;
+}
+
+}  // namespace pfk

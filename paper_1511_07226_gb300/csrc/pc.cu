@@ -1,0 +1,393 @@
+// Preconditioners B of the flexible methods (Sec. 2; notation table Sec. 3).
+//
+//  * Jacobi:     B(v) = D^-1 v.
+//  * Inner PCG:  k iterations of Alg. 3 (M^-1 = D^-1) on A y = v from y = 0,
+//                the inner solver of the paper's block-Jacobi experiments
+//                (Sec. 6, "5 iterations of Jacobi-preconditioned CG").
+//                Three kernels per inner iteration:
+//                  A_i  r_i = r_{i-1} - alpha_{i-1} s_{i-1}, partial gamma_i = <D^-1 r_i, r_i>
+//                  B_i  x_i = x_{i-1} + alpha_{i-1} p_{i-1}, p_i = D^-1 r_i + beta_i p_{i-1}
+//                  C_i  s_i = A p_i, partial eta_i = <s_i, p_i>
+//                each ending in a device-side last-block combine of its partial
+//                sums, so no host synchronisation happens inside B.
+//  * Chebyshev:  k sweeps of Chebyshev acceleration of Jacobi over [lo, hi]
+//                (Saad, Iterative Methods for Sparse Linear Systems, 2nd ed.,
+//                Alg. 12.1), one fused kernel per sweep.
+//
+// Precision variants (spec mixed precision): vectors V = double or
+// float, coefficient storage C = double, float or bfloat16.  Inner products of
+// the FP32 variants accumulate per thread in FP32 and are combined across
+// threads and blocks in FP64.
+#include "pfk_internal.cuh"
+
+#include <cmath>
+
+namespace pfk {
+
+pfk_status ensure_reduced_copies(pfk_operator* op, int precision);
+
+template <typename C>
+__device__ __forceinline__ double to_d(C v) { return (double)v; }
+template <>
+__device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <typename V, typename C>
+__device__ __forceinline__ V cv(C v) { return (V)v; }
+template <>
+__device__ __forceinline__ float cv<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename V, typename C>
+struct StencilT {
+  const C* d;
+  const C* kx;
+  const C* ky;
+  const C* kz;
+  const C* dinv;
+  int nx, ny, nz, ndim;
+  V a0, a1, a2;
+  int u0, u1, u2;
+  int64_t n;
+};
+
+template <typename V, typename C>
+__device__ __forceinline__ V stencil_row_t(const StencilT<V, C>& A, const V* __restrict__ m, int64_t c) {
+  const int64_t sxy = (int64_t)A.nx * A.ny;
+  const int i = (int)(c % A.nx);
+  const int j = (int)((c / A.nx) % A.ny);
+  V acc = cv<V, C>(A.d[c]) * m[c];
+  if (i > 0) acc -= (cv<V, C>(A.kx[c - 1]) + (A.u0 == -1 ? A.a0 : V(0))) * m[c - 1];
+  if (i < A.nx - 1) acc -= (cv<V, C>(A.kx[c]) + (A.u0 == 1 ? A.a0 : V(0))) * m[c + 1];
+  if (j > 0) acc -= (cv<V, C>(A.ky[c - A.nx]) + (A.u1 == -1 ? A.a1 : V(0))) * m[c - A.nx];
+  if (j < A.ny - 1) acc -= (cv<V, C>(A.ky[c]) + (A.u1 == 1 ? A.a1 : V(0))) * m[c + A.nx];
+  if (A.ndim == 3) {
+    const int k = (int)(c / sxy);
+    if (k > 0) acc -= (cv<V, C>(A.kz[c - sxy]) + (A.u2 == -1 ? A.a2 : V(0))) * m[c - sxy];
+    if (k < A.nz - 1) acc -= (cv<V, C>(A.kz[c]) + (A.u2 == 1 ? A.a2 : V(0))) * m[c + sxy];
+  }
+  return acc;
+}
+
+#define GRID_LOOP(c, n) \
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (n); c += (int64_t)gridDim.x * blockDim.x)
+
+#define SKIP_IF_DONE(status) \
+  if ((status) && *(status) != kRun) return;
+
+// ---------------------------------------------------------------------------
+// Jacobi / identity
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) jacobi_kernel(const double* __restrict__ dinv, const double* __restrict__ v,
+                                                          const double* __restrict__ add, double* __restrict__ out,
+                                                          int64_t n, const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  GRID_LOOP(c, n) {
+    double y = dinv ? dinv[c] * v[c] : v[c];
+    out[c] = add ? add[c] + y : y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inner Jacobi-PCG
+// ---------------------------------------------------------------------------
+
+// A_i.  i = 0: r_0 = v.  i >= 1: r_i = r_{i-1} - alpha_{i-1} s_{i-1}.
+// Finalize: gamma_0, or beta_i = gamma_i / gamma_{i-1} (stop if gamma_i == 0).
+template <typename V, typename C>
+__global__ void __launch_bounds__(kThreads) pcg_a_kernel(StencilT<V, C> A, const double* __restrict__ v,
+                                                         V* __restrict__ r, const V* __restrict__ s, PcCtl* ctl,
+                                                         int i, int k, double* partials,
+                                                         const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  const int last_x = ctl->ok;
+  if (i >= 1 && i > last_x) return;
+  const V alpha = i >= 1 ? (V)ctl->alpha[i - 1] : V(0);
+  V accv = V(0);
+  GRID_LOOP(c, A.n) {
+    V rv = (i == 0) ? (V)v[c] : r[c] - alpha * s[c];
+    r[c] = rv;
+    accv += (cv<V, C>(A.dinv[c]) * rv) * rv;
+  }
+  double acc[1] = {(double)accv};
+  __shared__ double smem[kThreads / 32];
+  __shared__ double sums[1];
+  if (reduce_last_block<1>(acc, 1, partials, 1, &ctl->counter, smem, sums) && threadIdx.x == 0) {
+    const double g = sums[0];
+    if (i == 0) {
+      ctl->gamma = g;
+      ctl->ok = (g == 0.0) ? 0 : k;
+    } else if (g == 0.0) {
+      ctl->ok = i;
+    } else {
+      ctl->beta[i] = g / ctl->gamma;
+      ctl->gamma = g;
+    }
+  }
+}
+
+// B_i.  x_i = x_{i-1} + alpha_{i-1} p_{i-1} (i >= 1, while i <= last_x);
+//       p_i = D^-1 r_i + beta_i p_{i-1} (p_0 = D^-1 r_0), while i < last_x.
+template <typename V, typename C>
+__global__ void __launch_bounds__(kThreads) pcg_b_kernel(StencilT<V, C> A, const V* __restrict__ r,
+                                                         const V* __restrict__ pold, V* __restrict__ pnew,
+                                                         V* __restrict__ x, PcCtl* ctl, int i,
+                                                         const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  const int last_x = ctl->ok;
+  const bool do_x = i >= 1 && i <= last_x;
+  const bool do_p = i < last_x;
+  if (!do_x && !do_p) return;
+  const V alpha = i >= 1 ? (V)ctl->alpha[i - 1] : V(0);
+  const V beta = i >= 1 ? (V)ctl->beta[i] : V(0);
+  GRID_LOOP(c, A.n) {
+    V po = i >= 1 ? pold[c] : V(0);
+    if (do_x) x[c] = (i == 1 ? V(0) : x[c]) + alpha * po;
+    if (do_p) pnew[c] = cv<V, C>(A.dinv[c]) * r[c] + beta * po;
+  }
+}
+
+// C_i.  s_i = A p_i, eta_i = <s_i, p_i>; finalize alpha_i = gamma_i / eta_i
+// (stop if eta_i == 0).
+template <typename V, typename C>
+__global__ void __launch_bounds__(kThreads) pcg_c_kernel(StencilT<V, C> A, const V* __restrict__ p,
+                                                         V* __restrict__ s, PcCtl* ctl, int i, double* partials,
+                                                         const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  if (!(i < ctl->ok)) return;
+  V accv = V(0);
+  GRID_LOOP(c, A.n) {
+    V sv = stencil_row_t<V, C>(A, p, c);
+    s[c] = sv;
+    accv += sv * p[c];
+  }
+  double acc[1] = {(double)accv};
+  __shared__ double smem[kThreads / 32];
+  __shared__ double sums[1];
+  if (reduce_last_block<1>(acc, 1, partials, 1, &ctl->counter, smem, sums) && threadIdx.x == 0) {
+    const double e = sums[0];
+    if (e == 0.0) {
+      ctl->ok = i;
+    } else {
+      ctl->eta = e;
+      ctl->alpha[i] = ctl->gamma / e;
+    }
+  }
+}
+
+// F.  x_k = x_{k-1} + alpha_{k-1} p_{k-1} if the loop reached iteration k;
+//     out = add + x.
+template <typename V, typename C>
+__global__ void __launch_bounds__(kThreads) pcg_final_kernel(int64_t n, const V* __restrict__ p,
+                                                             const V* __restrict__ x, const double* __restrict__ add,
+                                                             double* __restrict__ out, const PcCtl* ctl, int k,
+                                                             const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  const int last_x = ctl->ok;
+  const V alpha = (V)ctl->alpha[k - 1];
+  GRID_LOOP(c, n) {
+    double y;
+    if (last_x == 0) {
+      y = 0.0;
+    } else if (k <= last_x) {
+      y = (double)((k == 1 ? V(0) : x[c]) + alpha * p[c]);
+    } else {
+      y = (double)x[c];
+    }
+    out[c] = add ? add[c] + y : y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev-Jacobi
+// ---------------------------------------------------------------------------
+
+// Sweep 0 setup: r_0 = v, d_0 = (D^-1 r_0) / theta.
+template <typename V, typename C>
+__global__ void __launch_bounds__(kThreads) cheb_init_kernel(StencilT<V, C> A, const double* __restrict__ v,
+                                                             V* __restrict__ r, V* __restrict__ dvec, V theta,
+                                                             const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  GRID_LOOP(c, A.n) {
+    V rv = (V)v[c];
+    r[c] = rv;
+    dvec[c] = (cv<V, C>(A.dinv[c]) * rv) / theta;
+  }
+}
+
+// Sweep j (j + 1 < k): x_{j+1} = x_j + d_j; r_{j+1} = r_j - A d_j;
+// d_{j+1} = c1 d_j + c2 D^-1 r_{j+1}.  The last sweep only updates x and
+// writes out = add + x_k.
+template <typename V, typename C>
+__global__ void __launch_bounds__(kThreads) cheb_sweep_kernel(StencilT<V, C> A, const V* __restrict__ dj,
+                                                              V* __restrict__ dn, V* __restrict__ r,
+                                                              V* __restrict__ x, int j, int last, V c1, V c2,
+                                                              const double* __restrict__ add,
+                                                              double* __restrict__ out,
+                                                              const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  GRID_LOOP(c, A.n) {
+    const V dc = dj[c];
+    const V xv = (j == 0 ? V(0) : x[c]) + dc;
+    if (last) {
+      out[c] = add ? add[c] + (double)xv : (double)xv;
+    } else {
+      x[c] = xv;
+      const V rv = r[c] - stencil_row_t<V, C>(A, dj, c);
+      r[c] = rv;
+      dn[c] = c1 * dc + c2 * (cv<V, C>(A.dinv[c]) * rv);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+template <typename V, typename C>
+static StencilT<V, C> make_stencil(const pfk_operator* op, const C* d, const C* kx, const C* ky, const C* kz,
+                                   const C* dinv) {
+  StencilT<V, C> A;
+  A.d = d; A.kx = kx; A.ky = ky; A.kz = kz; A.dinv = dinv;
+  A.nx = op->nx; A.ny = op->ny; A.nz = op->nz; A.ndim = op->ndim;
+  A.a0 = (V)op->adv[0]; A.a1 = (V)op->adv[1]; A.a2 = (V)op->adv[2];
+  A.u0 = op->upw[0]; A.u1 = op->upw[1]; A.u2 = op->upw[2];
+  A.n = op->n;
+  return A;
+}
+
+template <typename V, typename C>
+static cudaError_t inner_pcg(const pfk_pc* pc, StencilT<V, C> A, const double* v, double* out, const double* add,
+                             const int* status, cudaStream_t st) {
+  const int64_t n = A.n;
+  V* base = (V*)pc->buf;
+  V* r = base;
+  V* s = base + n;
+  V* x = base + 2 * n;
+  V* p[2] = {base + 3 * n, base + 4 * n};
+  const int k = pc->inner;
+  const int blocks = stream_blocks(pc->ctx, n, 2);
+  const int sblocks = stream_blocks(pc->ctx, n, 8);
+  PcCtl* ctl = pc->ctl;
+  pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, 0, k, pc->partials, status);
+  pcg_b_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, r, nullptr, p[0], x, ctl, 0, status);
+  pcg_c_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, p[0], s, ctl, 0, pc->partials, status);
+  for (int i = 1; i < k; ++i) {
+    pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, i, k, pc->partials, status);
+    pcg_b_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, r, p[(i - 1) & 1], p[i & 1], x, ctl, i, status);
+    pcg_c_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, p[i & 1], s, ctl, i, pc->partials, status);
+  }
+  pcg_final_kernel<V, C><<<sblocks, kThreads, 0, st>>>(n, p[(k - 1) & 1], x, add, out, ctl, k, status);
+  return cudaGetLastError();
+}
+
+template <typename V, typename C>
+static cudaError_t chebyshev(const pfk_pc* pc, StencilT<V, C> A, const double* v, double* out, const double* add,
+                             const int* status, cudaStream_t st) {
+  const int64_t n = A.n;
+  V* base = (V*)pc->buf;
+  V* r = base;
+  V* x = base + n;
+  V* dv[2] = {base + 2 * n, base + 3 * n};
+  const int k = pc->inner;
+  const int sblocks = stream_blocks(pc->ctx, n, 8);
+  const double theta = (pc->hi + pc->lo) / 2.0, delta = (pc->hi - pc->lo) / 2.0;
+  const double sigma1 = theta / delta;
+  double rho = 1.0 / sigma1;
+  cheb_init_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, v, r, dv[0], (V)theta, status);
+  for (int j = 0; j < k; ++j) {
+    const int last = (j + 1 == k);
+    const double rho_new = 1.0 / (2.0 * sigma1 - rho);
+    const V c1 = (V)(rho_new * rho), c2 = (V)(2.0 * rho_new / delta);
+    cheb_sweep_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, dv[j & 1], dv[(j + 1) & 1], r, x, j, last, c1, c2, add,
+                                                          out, status);
+    rho = rho_new;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pc_apply(const pfk_pc* pc, const double* v, double* out, const double* add, const int* status,
+                     cudaStream_t st) {
+  const pfk_operator* op = pc->op;
+  const int64_t n = op->n;
+  if (pc->kind == PFK_PC_NONE || pc->kind == PFK_PC_JACOBI) {
+    const double* dinv = pc->kind == PFK_PC_NONE ? nullptr : (op->rowptr && op->csr_dinv ? op->csr_dinv : op->dinv);
+    jacobi_kernel<<<stream_blocks(pc->ctx, n, 8), kThreads, 0, st>>>(dinv, v, add, out, n, status);
+    return cudaGetLastError();
+  }
+  if (pc->kind == PFK_PC_INNER_PCG) {
+    if (pc->precision == PFK_FP64)
+      return inner_pcg<double, double>(pc, make_stencil<double, double>(op, op->d, op->kx, op->ky, op->kz, op->dinv),
+                                       v, out, add, status, st);
+    if (pc->precision == PFK_FP32)
+      return inner_pcg<float, float>(pc, make_stencil<float, float>(op, op->d32, op->kx32, op->ky32, op->kz32,
+                                                                    op->dinv32), v, out, add, status, st);
+    return inner_pcg<float, __nv_bfloat16>(pc, make_stencil<float, __nv_bfloat16>(op, op->d16, op->kx16, op->ky16,
+                                                                                   op->kz16, op->dinv16),
+                                           v, out, add, status, st);
+  }
+  // Chebyshev
+  if (pc->precision == PFK_FP64)
+    return chebyshev<double, double>(pc, make_stencil<double, double>(op, op->d, op->kx, op->ky, op->kz, op->dinv), v,
+                                     out, add, status, st);
+  if (pc->precision == PFK_FP32)
+    return chebyshev<float, float>(pc, make_stencil<float, float>(op, op->d32, op->kx32, op->ky32, op->kz32,
+                                                                  op->dinv32), v, out, add, status, st);
+  return chebyshev<float, __nv_bfloat16>(pc, make_stencil<float, __nv_bfloat16>(op, op->d16, op->kx16, op->ky16,
+                                                                                op->kz16, op->dinv16),
+                                         v, out, add, status, st);
+}
+
+pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc* desc, pfk_pc* pc) {
+  pc->ctx = ctx;
+  pc->op = op;
+  pc->kind = desc->kind;
+  pc->inner = desc->inner_iters;
+  pc->precision = desc->precision;
+  const bool stencil = op->d != nullptr;
+  if (pc->kind < PFK_PC_NONE || pc->kind > PFK_PC_CHEBYSHEV) {
+    set_error(ctx, "unknown preconditioner kind");
+    return PFK_ERR_INVALID;
+  }
+  if ((pc->kind == PFK_PC_INNER_PCG || pc->kind == PFK_PC_CHEBYSHEV)) {
+    if (!stencil) {
+      set_error(ctx, "inner-iteration preconditioners need a stencil operator");
+      return PFK_ERR_INVALID;
+    }
+    if (pc->inner < 1 || pc->inner > 64) {
+      set_error(ctx, "inner_iters must be in [1, 64]");
+      return PFK_ERR_INVALID;
+    }
+    if (pc->precision < PFK_FP64 || pc->precision > PFK_BF16_COEF_FP32) {
+      set_error(ctx, "unknown precision");
+      return PFK_ERR_INVALID;
+    }
+    pfk_status s = ensure_reduced_copies(const_cast<pfk_operator*>(op), pc->precision);
+    if (s != PFK_OK) return s;
+    const size_t esz = pc->precision == PFK_FP64 ? sizeof(double) : sizeof(float);
+    pc->buf_bytes = 5 * (size_t)op->n * esz;
+    PFK_CUDA(ctx, cudaMallocAsync(&pc->buf, pc->buf_bytes, ctx->stream));
+    PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->ctl, sizeof(PcCtl), ctx->stream));
+    PFK_CUDA(ctx, cudaMemsetAsync(pc->ctl, 0, sizeof(PcCtl), ctx->stream));
+    PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->partials, (size_t)ctx->num_sms * 8 * sizeof(double), ctx->stream));
+    if (pc->kind == PFK_PC_CHEBYSHEV) {
+      if (desc->cheb_lo == 0.0 && desc->cheb_hi == 0.0) {
+        pc->lo = 0.1 * op->gersh;
+        pc->hi = 1.1 * op->gersh;
+      } else {
+        pc->lo = desc->cheb_lo;
+        pc->hi = desc->cheb_hi;
+      }
+      if (!(pc->hi > pc->lo) || !(pc->lo > 0.0)) {
+        set_error(ctx, "Chebyshev bounds must satisfy 0 < lo < hi");
+        return PFK_ERR_INVALID;
+      }
+    }
+  } else if (pc->kind == PFK_PC_JACOBI && !stencil && !op->csr_dinv) {
+    set_error(ctx, "Jacobi needs the operator diagonal");
+    return PFK_ERR_INVALID;
+  }
+  PFK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return PFK_OK;
+}
+
+}  // namespace pfk

@@ -1,0 +1,231 @@
+// Internal declarations of the pfk library (not part of the C ABI).
+//
+// Layout in HBM: every vector is a contiguous FP64 array of n entries in cell
+// order i + nx (j + ny k), 256-byte aligned (cudaMalloc).  Direction histories
+// (p, s, q, z for PIPEFCG) are rings of (mmax + 1) such vectors stored back to
+// back, slot of direction k = k mod (mmax + 1).  Scalars of the iteration live
+// in a device control block (SolveCtl) so that every kernel of an iteration has
+// the same arguments and one captured CUDA graph can be replayed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pfk.h"
+
+namespace pfk {
+
+constexpr int kThreads = 256;          // threads per block of the streaming kernels
+constexpr int kMaxDots = PFK_MAX_MMAX + 8;
+
+// Status codes kept in SolveCtl::status.
+enum DevStatus : int {
+  kRun = 0,
+  kConverged = 1,
+  kBreakdown = 2,       // eta_i <= 0 (or t < 0): restart from x
+  kMaxit = 3,
+  kFillBreakdown = 4,   // eta_0 <= 0 in a pipeline fill
+  kNonFinite = 5,
+};
+
+// Device control block of one solve.
+struct SolveCtl {
+  int status;
+  int it;          // iterations so far (all restarts)
+  int i;           // index of the last completed iteration since the last (re)start
+  int nw;          // size of the window W_i whose betas are in beta[]
+  int hist_len;
+  int hist_cap;
+  int maxit;
+  int mmax;
+  int truncation;
+  int norm;
+  int target_set;
+  int pad0;
+  double target;
+  double rtol, atol;
+  double rho0, rho;
+  double alpha, gamma, delta, eta;
+  double beta[PFK_MAX_MMAX];
+  double eta_ring[PFK_MAX_MMAX + 1];
+  double* history;         // device buffer hist_cap * PFK_HISTORY_FIELDS
+  unsigned int counter;    // arrival counter of the last-block reduction
+  int passes;              // fused passes that did work
+  double alg_bytes;        // their algorithmic HBM bytes
+  double alg_flops;        // their FP64 flops (FMA = 2)
+};
+
+// Control block of a preconditioner application (inner iterations).
+struct PcCtl {
+  int ok;                  // last inner iteration whose x update happens (k, or
+                           // earlier when <D^-1 r, r> or <s, p> hit exactly 0)
+  int pad;
+  double gamma, eta;
+  double alpha[64];
+  double beta[64];
+  unsigned int counter;
+  unsigned int pad1;
+};
+
+}  // namespace pfk
+
+// ---------------------------------------------------------------------------
+// Opaque handle types of the C ABI
+// ---------------------------------------------------------------------------
+
+struct pfk_context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;    // library-owned, only used to record CUDA graphs
+  int num_sms = 0;
+  std::string err;
+  // cached workspace of pfk_solve (grown on demand)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* scratch_partials = nullptr;   // reduction partials for standalone calls
+  unsigned int* scratch_counter = nullptr;
+  double* scratch_out = nullptr;
+};
+
+struct pfk_operator {
+  pfk_context* ctx = nullptr;
+  int kind = 0;
+  int storage = 0;
+  int nx = 0, ny = 0, nz = 0, ndim = 0;
+  int64_t n = 0;
+  // stencil, FP64: diagonal, +x/+y/+z face coefficients (0 on the boundary), D^-1
+  double* d = nullptr;
+  double* kx = nullptr;
+  double* ky = nullptr;
+  double* kz = nullptr;
+  double* dinv = nullptr;
+  double adv[3] = {0, 0, 0};    // h |v_d|
+  int upw[3] = {0, 0, 0};       // -1: upwind at -e_d (v_d > 0), +1: at +e_d, 0: none
+  double gersh = 0.0;           // max_i sum_j |a_ij| / a_ii
+  // reduced-precision copies (created on demand by preconditioners)
+  float* d32 = nullptr;
+  float* kx32 = nullptr;
+  float* ky32 = nullptr;
+  float* kz32 = nullptr;
+  float* dinv32 = nullptr;
+  __nv_bfloat16* d16 = nullptr;
+  __nv_bfloat16* kx16 = nullptr;
+  __nv_bfloat16* ky16 = nullptr;
+  __nv_bfloat16* kz16 = nullptr;
+  __nv_bfloat16* dinv16 = nullptr;
+  // CSR (kind CSR, or stencil with storage CSR)
+  int64_t nnz = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* colidx = nullptr;
+  double* vals = nullptr;
+  double* csr_dinv = nullptr;
+};
+
+struct pfk_pc {
+  pfk_context* ctx = nullptr;
+  const pfk_operator* op = nullptr;
+  int kind = 0;
+  int inner = 0;
+  int precision = 0;
+  double lo = 0.0, hi = 0.0;
+  // scratch of the inner iterations (FP64 or FP32 depending on precision)
+  void* buf = nullptr;
+  size_t buf_bytes = 0;
+  pfk::PcCtl* ctl = nullptr;
+  double* partials = nullptr;
+};
+
+namespace pfk {
+
+// ---------------------------------------------------------------------------
+// Error handling helpers (host)
+// ---------------------------------------------------------------------------
+void set_error(pfk_context* ctx, const std::string& msg);
+pfk_status cuda_fail(pfk_context* ctx, cudaError_t e, const char* what);
+
+#define PFK_CUDA(ctx, call)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return pfk::cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+// Grid size of the streaming kernels: a fixed function of n and the SM count,
+// so reductions are combined in the same order on every run.
+int stream_blocks(const pfk_context* ctx, int64_t n, int blocks_per_sm = 2);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-level partial sums of `nd` accumulators, written to
+// partials[blockIdx.x * stride + j]; then the last block to arrive combines all
+// blocks' partials in a fixed order (lane-strided over blocks, then a fixed
+// shuffle tree) into sums[j] (shared memory of the last block).
+// Returns true in the last block (all its threads).  `smem` must hold
+// (kThreads / 32) * nd doubles; sums must hold nd doubles.
+template <int ND>
+__device__ __forceinline__ bool reduce_last_block(const double (&acc)[ND], int nd, double* partials, int stride,
+                                                  unsigned int* counter, double* smem, double* sums) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    if (j < nd) {
+      double v = warp_sum(acc[j]);
+      if (lane == 0) smem[warp * nd + j] = v;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += smem[w * nd + j];
+    partials[(size_t)blockIdx.x * stride + j] = v;
+  }
+  __shared__ unsigned int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  const int nb = gridDim.x;
+  for (int j = warp; j < nd; j += nwarps) {
+    double v = 0.0;
+    for (int b = lane; b < nb; b += 32) v += __ldcg(&partials[(size_t)b * stride + j]);
+    v = warp_sum(v);
+    if (lane == 0) sums[j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers shared between translation units
+// ---------------------------------------------------------------------------
+
+// y = A x (FP64).  If `status` is non-null the kernel does nothing when
+// *status != kRun.  If `bsub` is non-null computes y = bsub - A x.
+cudaError_t op_apply(const pfk_operator* op, const double* x, double* y, const double* bsub, const int* status,
+                     cudaStream_t st);
+
+// out = add + B(v) (add may be null).  `status` as above.
+cudaError_t pc_apply(const pfk_pc* pc, const double* v, double* out, const double* add, const int* status,
+                     cudaStream_t st);
+
+// Sum of squares / dot products into a device scalar (deterministic order).
+cudaError_t dot_into(pfk_context* ctx, const double* a, const double* b, int64_t n, double* out, cudaStream_t st);
+
+}  // namespace pfk

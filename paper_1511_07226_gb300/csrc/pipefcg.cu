@@ -1,0 +1,304 @@
+// PIPEFCG (Alg. 8) and naive PIPEFCG (Alg. 7) on one GPU.
+//
+// One iteration i is three kernel groups, all reading their scalars from the
+// device control block (no host synchronisation, capturable in a CUDA graph):
+//
+//  1. pipefcg_pass<NW>  one HBM pass that
+//       - finishes iteration i-1's four MAXPYs
+//           p_{i-1} = u_{i-1} + sum beta_{i-1,k} p_k,  s, q, z likewise,
+//         over the window W_{i-1} and writes them into ring slot (i-1) mod (mmax+1),
+//       - advances x_i, r_i, u_i (= tilde-u_i), w_i with alpha_{i-1},
+//       - accumulates the partial sums of gamma_i = <u_i, r_i>,
+//         delta_i = <u_i, w_i>, ||r_i||^2 and <u_i, s_k> for every s_k of
+//         W_{i-1} and s_{i-1} (the s_k are still in registers from the MAXPY),
+//       - writes the preconditioner input t = w_i - r_i (eq. BwMinusR),
+//       - and, in the last block to finish, combines the partial sums in a fixed
+//         order and computes beta_{i,k} = -<u_i, s_k>/eta_k,
+//         eta_i = delta_i - sum beta_{i,k}^2 eta_k, alpha_i = gamma_i/eta_i and the
+//         convergence / breakdown status (the single reduction phase of Alg. 8);
+//  2. the preconditioner, m_i = u_i + B(w_i - r_i) (Alg. 7: m_i = B(w_i));
+//  3. the operator, n_i = A m_i.
+//
+// The reduction of step 1 is "in flight" (its scalars are not needed) while
+// steps 2 and 3 run: the overlap the paper obtains with MPI_Iallreduce becomes
+// the absence of any host round trip between the passes.  The statement-level
+// arithmetic is the listing's; only kernel boundaries are moved: the MAXPYs of
+// iteration i-1 are deferred into the pass that starts iteration i.
+#include "pfk_internal.cuh"
+#include "solver.cuh"
+
+#include <cmath>
+
+namespace pfk {
+
+struct FcgArgs {
+  double* x;
+  double* r;
+  double* u;
+  double* w;
+  const double* m;
+  const double* n;
+  double* t;
+  double* P;
+  double* S;
+  double* Q;
+  double* Z;
+  int64_t N;
+  int mmax;
+  int naive;
+  SolveCtl* ctl;
+  double* partials;
+};
+
+__device__ __forceinline__ int nu_window(int i, int mmax, int truncation) {
+  return truncation == PFK_TRUNC_RESTART ? ((i - 1) % mmax) + 1 : (i < mmax ? i : mmax);
+}
+
+__device__ __forceinline__ void push_history(SolveCtl* c, double rho, double rn, double eta, double alpha) {
+  if (c->history && c->hist_len < c->hist_cap) {
+    double* h = c->history + (size_t)c->hist_len * PFK_HISTORY_FIELDS;
+    h[0] = rho; h[1] = rn; h[2] = eta; h[3] = alpha;
+  }
+  c->hist_len += 1;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(kThreads, 1) pipefcg_pass(FcgArgs a) {
+  SolveCtl* ctl = a.ctl;
+  if (ctl->status != kRun) return;
+  constexpr int ND = NW + 4;
+  __shared__ double s_beta[NW];
+  __shared__ size_t s_off[NW];
+  __shared__ double s_red[(kThreads / 32) * ND];
+  __shared__ double s_sum[ND];
+  const int iprev = ctl->i;      // i - 1
+  const int nwp = ctl->nw;       // |W_{i-1}|
+  const double alpha = ctl->alpha;
+  const int slots = a.mmax + 1;
+  const int64_t N = a.N;
+  if (threadIdx.x < nwp) {
+    const int k = iprev - nwp + (int)threadIdx.x;
+    s_beta[threadIdx.x] = ctl->beta[threadIdx.x];
+    s_off[threadIdx.x] = (size_t)(k % slots) * (size_t)N;
+  }
+  __syncthreads();
+  const size_t coff = (size_t)(iprev % slots) * (size_t)N;
+
+  double acc[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) acc[j] = 0.0;
+
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const double u0 = a.u[e], w0 = a.w[e];
+    double p = u0, s = w0, q = a.m[e], z = a.n[e];
+    double sk[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      if (j < nwp) {
+        const size_t o = s_off[j] + e;
+        const double b = s_beta[j];
+        const double sv = a.S[o];
+        p = fma(b, a.P[o], p);
+        s = fma(b, sv, s);
+        q = fma(b, a.Q[o], q);
+        z = fma(b, a.Z[o], z);
+        sk[j] = sv;
+      }
+    }
+    a.P[coff + e] = p;
+    a.S[coff + e] = s;
+    a.Q[coff + e] = q;
+    a.Z[coff + e] = z;
+    const double xn = fma(alpha, p, a.x[e]);
+    const double rn = fma(-alpha, s, a.r[e]);
+    const double un = fma(-alpha, q, u0);
+    const double wn = fma(-alpha, z, w0);
+    a.x[e] = xn;
+    a.r[e] = rn;
+    a.u[e] = un;
+    a.w[e] = wn;
+    if (!a.naive) a.t[e] = wn - rn;
+    acc[0] = fma(un, rn, acc[0]);
+    acc[1] = fma(un, wn, acc[1]);
+    acc[2] = fma(rn, rn, acc[2]);
+    acc[3] = fma(un, s, acc[3]);
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+      if (j < nwp) acc[4 + j] = fma(un, sk[j], acc[4 + j]);
+  }
+
+  if (!reduce_last_block<ND>(acc, nwp + 4, a.partials, ND, &ctl->counter, s_red, s_sum)) return;
+  if (threadIdx.x != 0) return;
+
+  // ---- scalar phase of iteration i (one thread) ----
+  const int i = iprev + 1;
+  const double gamma = s_sum[0], delta = s_sum[1], rr = s_sum[2];
+  // algorithmic traffic of this pass: u, w, m, n, x, r and 4 nu_{i-1} history
+  // vectors read; p, s, q, z, x, r, u, w (and t) written.  FP64 flops: 4 nu
+  // MAXPY FMAs, 4 advance FMAs, nu + 4 dot FMAs, and the subtraction for t.
+  ctl->passes += 1;
+  ctl->alg_bytes += 8.0 * (double)N * (double)(4 * nwp + 14 + (a.naive ? 0 : 1));
+  ctl->alg_flops += (double)N * (2.0 * (5 * nwp + 8) + (a.naive ? 0.0 : 1.0));
+  ctl->it += 1;
+  ctl->i = i;
+  ctl->gamma = gamma;
+  ctl->delta = delta;
+  const double rnorm = sqrt(rr);
+  const double rho = ctl->norm == PFK_NORM_NATURAL ? sqrt(fabs(gamma)) : rnorm;
+  ctl->rho = rho;
+  const int hslot = ctl->hist_len;
+  push_history(ctl, rho, rnorm, nan(""), nan(""));
+  if (!isfinite(rho)) { ctl->status = kNonFinite; return; }
+  if (rho <= ctl->target) { ctl->status = kConverged; return; }
+  const int nu = nu_window(i, a.mmax, ctl->truncation);
+  const int off = nwp + 1 - nu;     // position of k = i - nu among (W_{i-1}, i-1)
+  double sumb = 0.0;
+  for (int jj = 0; jj < nu; ++jj) {
+    const int src = off + jj;        // 0..nwp-1: W_{i-1}; nwp: s_{i-1}
+    const double c = src < nwp ? s_sum[4 + src] : s_sum[3];
+    const int k = i - nu + jj;
+    const double ek = ctl->eta_ring[k % slots];
+    const double b = -c / ek;
+    ctl->beta[jj] = b;
+    sumb += b * b * ek;
+  }
+  const double eta = delta - sumb;
+  const double al = eta != 0.0 ? gamma / eta : nan("");
+  ctl->eta = eta;
+  ctl->alpha = al;
+  ctl->nw = nu;
+  ctl->eta_ring[i % slots] = eta;
+  if (ctl->history && hslot < ctl->hist_cap) {
+    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 2] = eta;
+    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 3] = al;
+  }
+  if (eta <= 0.0) { ctl->status = kBreakdown; return; }
+  if (ctl->it >= ctl->maxit) { ctl->status = kMaxit; return; }
+}
+
+// Pipeline fill dots: gamma_0 = <u_0, r_0>, delta_0 = <u_0, w_0>, ||r_0||^2,
+// then eta_0 = delta_0, alpha_0 = gamma_0 / eta_0 and the fill status.
+__global__ void __launch_bounds__(kThreads) pipefcg_fill_dots(const double* __restrict__ u,
+                                                              const double* __restrict__ r,
+                                                              const double* __restrict__ w, int64_t N,
+                                                              SolveCtl* ctl, double* partials) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const double uv = u[e], rv = r[e];
+    acc[0] = fma(uv, rv, acc[0]);
+    acc[1] = fma(uv, w[e], acc[1]);
+    acc[2] = fma(rv, rv, acc[2]);
+  }
+  __shared__ double s_red[(kThreads / 32) * 3];
+  __shared__ double s_sum[3];
+  if (!reduce_last_block<3>(acc, 3, partials, 3, &ctl->counter, s_red, s_sum)) return;
+  if (threadIdx.x != 0) return;
+  const double gamma = s_sum[0], delta = s_sum[1];
+  const double rnorm = sqrt(s_sum[2]);
+  const double rho = ctl->norm == PFK_NORM_NATURAL ? sqrt(fabs(gamma)) : rnorm;
+  if (!ctl->target_set) {
+    ctl->rho0 = rho;
+    ctl->target = fmax(ctl->rtol * rho, ctl->atol);
+    ctl->target_set = 1;
+  }
+  const double eta = delta;
+  const double al = eta != 0.0 ? gamma / eta : nan("");
+  push_history(ctl, rho, rnorm, eta, al);
+  ctl->rho = rho;
+  ctl->gamma = gamma;
+  ctl->delta = delta;
+  ctl->eta = eta;
+  ctl->alpha = al;
+  ctl->i = 0;
+  ctl->nw = 0;
+  ctl->eta_ring[0] = eta;
+  if (!isfinite(rho)) ctl->status = kNonFinite;
+  else if (rho <= ctl->target) ctl->status = kConverged;
+  else if (eta <= 0.0) ctl->status = kFillBreakdown;
+  else ctl->status = kRun;
+}
+
+template <int NW>
+static cudaError_t launch_pass(const FcgArgs& a, int blocks, cudaStream_t st) {
+  pipefcg_pass<NW><<<blocks, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_pass_any(const FcgArgs& a, int nw_template, int blocks, cudaStream_t st) {
+  switch (nw_template) {
+    case 4: return launch_pass<4>(a, blocks, st);
+    case 8: return launch_pass<8>(a, blocks, st);
+    case 16: return launch_pass<16>(a, blocks, st);
+    default: return launch_pass<32>(a, blocks, st);
+  }
+}
+
+int pipefcg_template(int mmax) { return mmax <= 4 ? 4 : mmax <= 8 ? 8 : mmax <= 16 ? 16 : 32; }
+
+// --------------------------------------------------------------------------
+// Method object
+// --------------------------------------------------------------------------
+
+class PipeFcg : public Method {
+ public:
+  PipeFcg(bool naive) : naive_(naive) {}
+
+  int64_t workspace_doubles(int64_t N, int mmax) const override {
+    return 7 * N + 4 * (int64_t)(mmax + 1) * N;
+  }
+
+  void bind(double* ws, int64_t N, int mmax) override {
+    N_ = N;
+    mmax_ = mmax;
+    r_ = ws; u_ = r_ + N; w_ = u_ + N; m_ = w_ + N; n_ = m_ + N; t_ = n_ + N; tmp_ = t_ + N;
+    P_ = tmp_ + N;
+    S_ = P_ + (mmax + 1) * N;
+    Q_ = S_ + (mmax + 1) * N;
+    Z_ = Q_ + (mmax + 1) * N;
+  }
+
+  double* scratch() override { return tmp_; }
+
+  cudaError_t fill(const SolveEnv& env, const double* b, double* x) override {
+    cudaStream_t st = env.st;
+    cudaError_t e;
+    if ((e = op_apply(env.op, x, r_, b, nullptr, st)) != cudaSuccess) return e;          // r_0 = b - A x_0
+    if ((e = env.pc_apply(r_, u_, nullptr, nullptr)) != cudaSuccess) return e;           // u_0 = B(r_0)
+    if ((e = op_apply(env.op, u_, w_, nullptr, nullptr, st)) != cudaSuccess) return e;  // w_0 = A p_0, p_0 = u_0
+    if ((e = env.pc_apply(w_, m_, nullptr, nullptr)) != cudaSuccess) return e;           // m_0 = B(w_0)
+    if ((e = op_apply(env.op, m_, n_, nullptr, nullptr, st)) != cudaSuccess) return e;   // n_0 = A m_0
+    pipefcg_fill_dots<<<stream_blocks(env.ctx, N_, 2), kThreads, 0, st>>>(u_, r_, w_, N_, env.ctl, env.partials);
+    return cudaGetLastError();
+  }
+
+  cudaError_t iteration(const SolveEnv& env, double* x) override {
+    FcgArgs a;
+    a.x = x; a.r = r_; a.u = u_; a.w = w_; a.m = m_; a.n = n_; a.t = t_;
+    a.P = P_; a.S = S_; a.Q = Q_; a.Z = Z_;
+    a.N = N_; a.mmax = mmax_; a.naive = naive_ ? 1 : 0;
+    a.ctl = env.ctl; a.partials = env.partials;
+    const int tmpl = pipefcg_template(mmax_);
+    cudaError_t e = env.mark_pass(0);
+    if (e != cudaSuccess) return e;
+    e = launch_pass_any(a, tmpl, stream_blocks(env.ctx, N_, 1), env.st);
+    if (e != cudaSuccess) return e;
+    if ((e = env.mark_pass(1)) != cudaSuccess) return e;
+    const int* status = &env.ctl->status;
+    if (naive_) e = env.pc_apply(w_, m_, nullptr, status);      // m_i = B(w_i)          (Alg. 7)
+    else e = env.pc_apply(t_, m_, u_, status);                   // m_i = u_i + B(w_i - r_i) (Alg. 8)
+    if (e != cudaSuccess) return e;
+    return op_apply(env.op, m_, n_, nullptr, status, env.st);    // n_i = A m_i
+  }
+
+ private:
+  bool naive_;
+  int64_t N_ = 0;
+  int mmax_ = 0;
+  double *r_ = nullptr, *u_ = nullptr, *w_ = nullptr, *m_ = nullptr, *n_ = nullptr, *t_ = nullptr,
+         *tmp_ = nullptr;
+  double *P_ = nullptr, *S_ = nullptr, *Q_ = nullptr, *Z_ = nullptr;
+};
+
+Method* make_pipefcg(bool naive) { return new PipeFcg(naive); }
+
+}  // namespace pfk

@@ -1,0 +1,157 @@
+"""PIPEFCG (Alg. 8) and naive PIPEFCG (Alg. 7) on the GPU against the oracle.
+
+Whole solves are compared with the protocol of tests/_parity.py: 1e-10 on every
+iteration of the prefix where the oracle's own rounding envelope is below
+1e-11, within 100x that envelope while the trajectories stay correlated, and
+the same status, iteration count band and true residual."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov as K
+from oracle import operators as O
+from oracle import preconditioners as PC
+from tests._parity import check_solve, oracle_with_envelope
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    from paper_1511_07226_gb300 import pfk
+    return pfk.Context(0)
+
+
+def test_config1_csr_jacobi(ctx):
+    """2D 64x64, 8 inclusions of 1e3, FP64 CSR, Jacobi, PIPEFCG nu_max = 30, rtol 1e-8."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson2d_inclusions()
+    aop = O.StencilOperator(c["dims"], c["eta"]).to_csr()
+    prm = K.Params(mmax=30, rtol=1e-8)
+    ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.JacobiPC(aop), c["b"], prm)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"], storage="csr")
+    pc = pfk.Preconditioner(ctx, op, "jacobi")
+    x, info, hist = pfk.solve(ctx, op, pc, c["b"], method="pipefcg", mmax=30, rtol=1e-8, history=4000)
+    s = check_solve(hist, info, ref, alts, rtol=1e-8)
+    assert s["prefix"] >= 30
+    a = sp.csr_matrix((aop.vals, aop.colidx, aop.rowptr), shape=(aop.n, aop.n))
+    xs = spl.spsolve(a.tocsc(), c["b"])
+    e_gpu = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+    e_ora = np.linalg.norm(ref.x - xs) / np.linalg.norm(xs)
+    assert e_gpu <= 10 * e_ora + 1e-12
+
+
+@pytest.mark.parametrize("method", ["pipefcg", "pipefcg_naive"])
+@pytest.mark.parametrize("mmax,trunc", [(30, "standard"), (5, "standard"), (4, "restart"), (1, "standard")])
+def test_3d_inner_pcg(ctx, method, mmax, trunc):
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(dims=(20, 18, 14), ell=4.0, log_contrast=2.0, config_id=2, item_id=5)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    prm = K.Params(mmax=mmax, rtol=1e-8, truncation=trunc, maxit=300)
+    ref, alts = oracle_with_envelope(method, aop, lambda: PC.InnerPCG(aop, 4), c["b"], prm)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
+    x, info, hist = pfk.solve(ctx, op, pc, c["b"], method=method, mmax=mmax, truncation=trunc, rtol=1e-8,
+                              maxit=300, history=4000)
+    check_solve(hist, info, ref, alts, rtol=1e-8)
+
+
+def test_unpreconditioned_norm_and_maxit(ctx):
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(dims=(16, 16, 16), ell=4.0, log_contrast=3.0, config_id=2, item_id=6)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    prm = K.Params(mmax=30, rtol=1e-12, norm="unpreconditioned", maxit=25)
+    ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.JacobiPC(aop), c["b"], prm)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], method="pipefcg",
+                              mmax=30, rtol=1e-12, norm="unpreconditioned", maxit=25, history=100)
+    assert ref.status == "maxit" and info["status_name"] == "not_converged" and info["iterations"] == 25
+    s = check_solve(hist, info, ref, alts)
+    if s["prefix"] == len(hist):
+        assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+def test_bitwise_reproducible_and_device_path(ctx):
+    import torch
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(dims=(33, 29, 17), ell=4.0, log_contrast=3.0, config_id=2, item_id=7)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
+    x1, i1, h1 = pfk.solve(ctx, op, pc, c["b"], history=1000)
+    x2, i2, h2 = pfk.solve(ctx, op, pc, c["b"], history=1000)
+    assert np.array_equal(x1, x2) and np.array_equal(h1, h2, equal_nan=True)
+    bd = torch.from_numpy(c["b"]).cuda()
+    x3, i3, h3 = pfk.solve(ctx, op, pc, bd, history=1000)
+    assert np.array_equal(x3.cpu().numpy(), x1) and np.array_equal(h3, h1, equal_nan=True)
+    assert i1["status"] == 0 and i1["rnorm_true"] <= 1e-8 * i1["bnorm"]
+    # graph length does not change the arithmetic
+    x4, i4, h4 = pfk.solve(ctx, op, pc, c["b"], history=1000, graph_iters=3)
+    assert np.array_equal(x4, x1) and i4["iterations"] == i1["iterations"]
+
+
+def test_nonzero_initial_guess(ctx):
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(dims=(12, 11, 10), ell=3.0, log_contrast=1.0, config_id=2, item_id=8)
+    x0 = W.random_vector(len(c["b"]), 9) * 1e-3
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    prm = K.Params(mmax=10, rtol=1e-9)
+    ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.JacobiPC(aop), c["b"], prm, x0=x0)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], x0=x0, mmax=10, rtol=1e-9,
+                              history=500)
+    check_solve(hist, info, ref, alts, rtol=1e-9)
+
+
+def test_breakdown_restarts_match_oracle(ctx):
+    """Indefinite system: eta_i <= 0 restarts from x_i, then PFK_ERR_BREAKDOWN (Sec. 5)."""
+    from paper_1511_07226_gb300 import pfk
+    a = W.random_spd(30, cond=10.0, item_id=17)
+    b = W.random_vector(30, 17)
+    d = np.linalg.eigvalsh(a)
+    sh = a - (d[0] + 0.5 * (d[1] - d[0])) * np.eye(30)
+    rp = np.arange(0, 31 * 30, 30, dtype=np.int32)
+    ci = np.tile(np.arange(30, dtype=np.int32), 30)
+    ref = K.solve("pipefcg", O.DenseOperator(sh), PC.IdentityPC(), b,
+                  prm=K.Params(rtol=1e-8, mmax=30, max_restarts=3))
+    op = pfk.Operator.csr(ctx, rp, ci, sh.reshape(-1))
+    x, info, hist = pfk.solve(ctx, op, None, b, mmax=30, rtol=1e-8, max_restarts=3, history=200)
+    assert ref.status == "breakdown" and info["status_name"] == "breakdown"
+    assert info["breakdowns"] == ref.breakdowns == 4 and info["restarts"] == ref.restarts == 3
+
+
+def test_invalid_arguments(ctx):
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(dims=(8, 8, 8), ell=2.0, config_id=2, item_id=10)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    with pytest.raises(pfk.PfkError):
+        pfk.solve(ctx, op, None, c["b"], mmax=0)
+    with pytest.raises(pfk.PfkError):
+        pfk.solve(ctx, op, None, c["b"], mmax=33)
+    with pytest.raises(pfk.PfkError):
+        pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=0)
+
+
+@pytest.mark.slow
+def test_config2_full_size(ctx):
+    """128^3 (2.1M unknowns), contrast 1e6, 4 inner Jacobi-PCG, nu_max = 30: the
+    leading iterations against the oracle (strict prefix of the envelope), sampled
+    iterate entries, and the converged solve's true residual."""
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(n=128)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    prm = K.Params(mmax=30, rtol=1e-8, maxit=8)
+    ref = K.solve("pipefcg", aop, PC.InnerPCG(aop, 4), c["b"], prm=prm)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
+    x, info, hist = pfk.solve(ctx, op, pc, c["b"], mmax=30, rtol=1e-8, maxit=8, history=64)
+    rho = ref.rho()
+    assert len(hist) == len(rho)
+    d = np.abs(hist[:, 0] - rho) / rho
+    assert d.max() <= 1e-10, d
+    g = W.rng(960, 0)
+    idx = g.integers(0, len(x), size=4000)
+    assert np.allclose(x[idx], ref.x[idx], rtol=1e-9, atol=1e-12 * np.abs(ref.x).max())
+    x, info, hist = pfk.solve(ctx, op, pc, c["b"], mmax=30, rtol=1e-8, history=4000)
+    assert info["status"] == 0 and info["rnorm_true"] <= 1e-8 * info["bnorm"]
