@@ -286,6 +286,36 @@ int pfk_method_storage_vectors(int method, int mmax);
 pfk_status pfk_solve_workspace_bytes(int method, int mmax, int64_t n, int64_t* bytes);
 pfk_status pfk_pc_workspace_bytes(const pfk_pc* pc, int64_t* bytes);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free preconditioner application                                */
+/* ------------------------------------------------------------------------ */
+
+/* Largest operator size accepted by pfk_pc_apply_inner_pcg_noalloc. */
+#define PFK_NOALLOC_MAX_N 262144
+
+/* y = B(v) for the FP64 inner Jacobi-PCG preconditioner (the same result as
+ * pfk_pc_apply with a PFK_PC_INNER_PCG / PFK_FP64 preconditioner of
+ * `inner_iters` iterations on `op`), without allocating any device memory.
+ * The paper has no counterpart: this is a library service for callers that
+ * cannot allocate device memory at the point where they apply the
+ * preconditioner -- for instance a framework that has handed all device memory
+ * to its own pool allocator, or code that cannot tolerate the device-wide
+ * synchronisation cudaMalloc/cudaFree may imply.
+ *  - op: a stencil operator (created beforehand) of at most PFK_NOALLOC_MAX_N
+ *    unknowns; larger sizes return PFK_ERR_INVALID.  1 <= inner_iters <= 64.
+ *  - v, y: device pointers of length n; must not overlap.
+ *  - Scratch: one static device array of about 10.5 MB, present on every GPU
+ *    that loads the library until the process exits.  The first call on a
+ *    device looks up the array's device address (cudaGetSymbolAddress); make
+ *    that first call before any stream capture.
+ *  - Every call shares the array: calls that overlap on the GPU (other
+ *    streams, other host threads, other contexts on the same device) race and
+ *    give wrong results.  Each call clears the parts that must start at zero.
+ *  - Ordered on ctx's stream; returns after the work completes.
+ * Errors: PFK_ERR_INVALID, PFK_ERR_CUDA. */
+pfk_status pfk_pc_apply_inner_pcg_noalloc(pfk_context* ctx, const pfk_operator* op, int inner_iters,
+                                          const double* v, double* y);
+
 #ifdef __cplusplus
 }
 #endif

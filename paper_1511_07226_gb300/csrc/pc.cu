@@ -391,3 +391,98 @@ pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc
 }
 
 }  // namespace pfk
+
+// ---------------------------------------------------------------------------
+// Allocation-free inner Jacobi-PCG application (pfk_pc_apply_inner_pcg_noalloc)
+//
+// For callers that must not allocate device memory when they apply the
+// preconditioner.  The scratch of the inner iterations (five work vectors, the
+// per-block partial sums and the control block) lives in one file-scope device
+// array instead of pfk_pc's cudaMalloc'd buffers; the kernels are the same.
+// The array exists once per GPU that loads the library and stays allocated
+// until the process exits.  Host code cannot use the array's name as a device
+// address: its address is fetched per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace pfk {
+
+constexpr int64_t kNoallocMaxN = PFK_NOALLOC_MAX_N;
+constexpr int64_t kNoallocPartials = 2048;   // >= 2 blocks per SM on any current GPU
+constexpr int64_t kNoallocCtlDoubles = (sizeof(PcCtl) + sizeof(double) - 1) / sizeof(double);
+constexpr int64_t kNoallocDoubles = 5 * kNoallocMaxN + kNoallocPartials + kNoallocCtlDoubles;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+constexpr int kNoallocMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on ctx's device (looked up once per device).
+static pfk_status noalloc_scratch(pfk_context* ctx, double** out) {
+  if (ctx->device < 0 || ctx->device >= kNoallocMaxDevices) {
+    set_error(ctx, "device index too large for the allocation-free entry point");
+    return PFK_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[ctx->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress (static scratch)");
+    g_noalloc_addr[ctx->device] = (double*)p;
+  }
+  *out = g_noalloc_addr[ctx->device];
+  return PFK_OK;
+}
+
+}  // namespace pfk
+
+extern "C" pfk_status pfk_pc_apply_inner_pcg_noalloc(pfk_context* ctx, const pfk_operator* op, int inner_iters,
+                                                      const double* v, double* y) {
+  using namespace pfk;
+  if (!ctx || !op || !v || !y) {
+    set_error(ctx, "NULL argument");
+    return PFK_ERR_INVALID;
+  }
+  if (v == y) {
+    set_error(ctx, "v and y must not overlap");
+    return PFK_ERR_INVALID;
+  }
+  if (!op->d) {
+    set_error(ctx, "the allocation-free inner PCG needs a stencil operator");
+    return PFK_ERR_INVALID;
+  }
+  if (inner_iters < 1 || inner_iters > 64) {
+    set_error(ctx, "inner_iters must be in [1, 64]");
+    return PFK_ERR_INVALID;
+  }
+  if (op->n > kNoallocMaxN) {
+    set_error(ctx, "operator size exceeds PFK_NOALLOC_MAX_N (262144 unknowns), the capacity of the static "
+                   "scratch of the allocation-free entry point");
+    return PFK_ERR_INVALID;
+  }
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  double* scratch = nullptr;
+  pfk_status s = noalloc_scratch(ctx, &scratch);
+  if (s != PFK_OK) return s;
+  pfk_pc tmp;
+  tmp.ctx = ctx;
+  tmp.op = op;
+  tmp.kind = PFK_PC_INNER_PCG;
+  tmp.inner = inner_iters;
+  tmp.precision = PFK_FP64;
+  tmp.buf = scratch;
+  tmp.buf_bytes = 5 * (size_t)op->n * sizeof(double);
+  tmp.partials = scratch + 5 * kNoallocMaxN;
+  tmp.ctl = (PcCtl*)(scratch + 5 * kNoallocMaxN + kNoallocPartials);
+  // the control block keeps the previous call's values: its arrival counter
+  // must start at zero
+  PFK_CUDA(ctx, cudaMemsetAsync(tmp.ctl, 0, sizeof(PcCtl), ctx->stream));
+  const StencilT<double, double> A = make_stencil<double, double>(op, op->d, op->kx, op->ky, op->kz, op->dinv);
+  e = inner_pcg<double, double>(&tmp, A, v, y, nullptr, nullptr, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "inner PCG kernels");
+  PFK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return PFK_OK;
+}

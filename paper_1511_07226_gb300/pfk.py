@@ -85,6 +85,7 @@ _SIGS = {
     "pfk_method_storage_vectors": (C.c_int, [C.c_int, C.c_int]),
     "pfk_solve_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_int64)]),
     "pfk_pc_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "pfk_pc_apply_inner_pcg_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -325,6 +326,25 @@ def solve(ctx: Context, op: Operator, pc: Preconditioner | None, b, x0=None, his
     if hist is not None:
         hist = hist[:min(info.history_len, history)]
     return x, d, hist
+
+
+NOALLOC_MAX_N = 262144
+
+
+def pc_apply_inner_pcg_noalloc(ctx: Context, op: Operator, inner_iters: int, v, y=None):
+    """y = B(v), FP64 inner Jacobi-PCG, through the allocation-free entry point.
+
+    The library allocates nothing for this call (its scratch is a static device
+    array); `y` may be given preallocated (a CUDA float64 tensor), otherwise this
+    helper allocates it with torch before the call.
+    """
+    torch = _torch()
+    vd = _dev_f64(v, ctx.device)
+    if y is None:
+        y = torch.empty_like(vd)
+    _check(load().pfk_pc_apply_inner_pcg_noalloc(ctx.h, op.h, int(inner_iters), C.c_void_p(vd.data_ptr()),
+                                                 C.c_void_p(y.data_ptr())), ctx.h)
+    return y
 
 
 def storage_vectors(method: str, mmax: int) -> int:
