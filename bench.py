@@ -114,9 +114,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def make_problem():
+def make_problem(n: int = 128):
     import workloads as W
-    return W.poisson3d_gaussian(n=128)
+    return W.poisson3d_gaussian(n=n)
 
 
 def cpu_baseline(c, its: int, n_iter: int = 2) -> dict:
@@ -192,7 +192,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iterations", type=int, default=0,
                     help="iterations one solve takes (for the reference arm's extrapolation)")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="one solve of an n^3 problem with at most --maxit iterations, for profiler captures")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--maxit", type=int, default=10000)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     args = ap.parse_args()
+    if args.ncu_case:
+        from paper_1511_07226_gb300 import pfk
+        c = make_problem(args.n)
+        ctx = pfk.Context(0)
+        op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+        pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4, precision=args.precision)
+        _, info, _ = pfk.solve(ctx, op, pc, c["b"], method="pipefcg", mmax=30, rtol=1e-8, maxit=args.maxit)
+        print(json.dumps({"ncu_case": args.n, "iterations": info["iterations"], "status": info["status_name"]}))
+        return
     if args.ref_iterations <= 0:
         args.ref_iterations = REF_ITERATIONS
     if args.impl == "reference":
