@@ -48,8 +48,12 @@ WORKLOAD = "PIPEFCG nu_max=30, 3D 128^3 variable-coefficient Poisson (contrast 1
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic per launch of the fused pass from the committed ncu summary
-# (profiles/pipefcg_pass_128cube.md), valid while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha256": None, "bytes_per_launch": None}
+# (profiles/pipefcg_pass_96cube.md): one full-window launch (nu = 30) on 96^3,
+# 948.19 MB read + written against 955.51 MB algorithmic, scaled to 128^3 by
+# the number of unknowns.  Valid only while the kernel source is unchanged.
+NCU_TRAFFIC = {"source_sha256": "2926c08f6c107be0c3c44aedd9e4818ff7decc64c03a8aeb31567ea1a3eab6ae",
+               "bytes_per_launch": 2.2476e9, "alg_bytes_per_launch": 2.2649e9, "window": 30,
+               "captured_on": "96^3, scaled by 128^3/96^3"}
 
 
 def measured_peaks() -> dict:
@@ -278,8 +282,11 @@ def main():
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     traffic = None
+    traffic_note = "kernel changed since the ncu capture"
     if NCU_TRAFFIC["source_sha256"] == kernel_source_hash():
         traffic = NCU_TRAFFIC["bytes_per_launch"]
+        traffic_note = (f"full-window launch (nu = {NCU_TRAFFIC['window']}), {NCU_TRAFFIC['captured_on']}; "
+                        f"algorithmic bytes of that launch {NCU_TRAFFIC['alg_bytes_per_launch']:.4g}")
 
     # ---- end to end through the C ABI with host buffers ----
     bh = c["b"].copy()
@@ -330,7 +337,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
         "roofline": {"kernel": "pipefcg_pass<32> (fused MAXPY + advance + multi-dot)", "bound": "alu",
                      "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic, "traffic_note": traffic_note,
                      "peak_source": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (recipe's 1.25 TFLOP/s)",
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": achieved_gbs / hbm_peak, "avg_pass_ms": pass_ms,

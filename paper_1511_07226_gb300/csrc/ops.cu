@@ -141,31 +141,39 @@ struct StencilArgs {
   int64_t n;
 };
 
-__device__ __forceinline__ double stencil_row(const StencilArgs& A, const double* __restrict__ m, int64_t c) {
+__device__ __forceinline__ double stencil_row(const StencilArgs& A, const double* __restrict__ m, int64_t c, int i,
+                                              int j, int k) {
   const int64_t sxy = (int64_t)A.nx * A.ny;
-  const int i = (int)(c % A.nx);
-  const int j = (int)((c / A.nx) % A.ny);
   double acc = A.d[c] * m[c];
   if (i > 0) acc = fma(-(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)), m[c - 1], acc);
   if (i < A.nx - 1) acc = fma(-(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)), m[c + 1], acc);
   if (j > 0) acc = fma(-(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)), m[c - A.nx], acc);
   if (j < A.ny - 1) acc = fma(-(A.ky[c] + (A.u1 == 1 ? A.a1 : 0.0)), m[c + A.nx], acc);
   if (A.ndim == 3) {
-    const int k = (int)(c / sxy);
     if (k > 0) acc = fma(-(A.kz[c - sxy] + (A.u2 == -1 ? A.a2 : 0.0)), m[c - sxy], acc);
     if (k < A.nz - 1) acc = fma(-(A.kz[c] + (A.u2 == 1 ? A.a2 : 0.0)), m[c + sxy], acc);
   }
   return acc;
 }
 
+// Stencil kernels walk the grid one x-row per warp (lanes along x, coalesced);
+// the row index gives (j, k) with one 32-bit division per row.
 __global__ void __launch_bounds__(kThreads) stencil_apply_kernel(StencilArgs A, const double* __restrict__ m,
                                                                  double* __restrict__ y,
                                                                  const double* __restrict__ bsub,
                                                                  const int* __restrict__ status) {
   if (status && *status != kRun) return;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < A.n; c += (int64_t)gridDim.x * blockDim.x) {
-    double v = stencil_row(A, m, c);
-    y[c] = bsub ? bsub[c] - v : v;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int nrows = A.ny * A.nz;
+  for (int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); row < nrows; row += nwarps) {
+    const int j = row % A.ny, k = row / A.ny;
+    const int64_t base = (int64_t)row * A.nx;
+    for (int i = lane; i < A.nx; i += 32) {
+      const int64_t c = base + i;
+      const double v = stencil_row(A, m, c, i, j, k);
+      y[c] = bsub ? bsub[c] - v : v;
+    }
   }
 }
 

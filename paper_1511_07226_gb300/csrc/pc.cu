@@ -50,22 +50,28 @@ struct StencilT {
 };
 
 template <typename V, typename C>
-__device__ __forceinline__ V stencil_row_t(const StencilT<V, C>& A, const V* __restrict__ m, int64_t c) {
+__device__ __forceinline__ V stencil_row_t(const StencilT<V, C>& A, const V* __restrict__ m, int64_t c, int i, int j,
+                                           int k) {
   const int64_t sxy = (int64_t)A.nx * A.ny;
-  const int i = (int)(c % A.nx);
-  const int j = (int)((c / A.nx) % A.ny);
   V acc = cv<V, C>(A.d[c]) * m[c];
   if (i > 0) acc -= (cv<V, C>(A.kx[c - 1]) + (A.u0 == -1 ? A.a0 : V(0))) * m[c - 1];
   if (i < A.nx - 1) acc -= (cv<V, C>(A.kx[c]) + (A.u0 == 1 ? A.a0 : V(0))) * m[c + 1];
   if (j > 0) acc -= (cv<V, C>(A.ky[c - A.nx]) + (A.u1 == -1 ? A.a1 : V(0))) * m[c - A.nx];
   if (j < A.ny - 1) acc -= (cv<V, C>(A.ky[c]) + (A.u1 == 1 ? A.a1 : V(0))) * m[c + A.nx];
   if (A.ndim == 3) {
-    const int k = (int)(c / sxy);
     if (k > 0) acc -= (cv<V, C>(A.kz[c - sxy]) + (A.u2 == -1 ? A.a2 : V(0))) * m[c - sxy];
     if (k < A.nz - 1) acc -= (cv<V, C>(A.kz[c]) + (A.u2 == 1 ? A.a2 : V(0))) * m[c + sxy];
   }
   return acc;
 }
+
+// Stencil loops: one x-row per warp (lanes along x); (j, k) from the row index.
+#define ROW_LOOP(A, c, i, j, k)                                                                   \
+  for (int row_ = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), j = 0, k = 0;               \
+       row_ < (A).ny * (A).nz && ((j = row_ % (A).ny), (k = row_ / (A).ny), true);                 \
+       row_ += (int)((gridDim.x * blockDim.x) >> 5))                                               \
+    for (int i = (int)(threadIdx.x & 31); i < (A).nx; i += 32)                                     \
+      for (int64_t c = (int64_t)row_ * (A).nx + i, once_ = 1; once_; once_ = 0)
 
 #define GRID_LOOP(c, n) \
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (n); c += (int64_t)gridDim.x * blockDim.x)
@@ -155,8 +161,8 @@ __global__ void __launch_bounds__(kThreads) pcg_c_kernel(StencilT<V, C> A, const
   SKIP_IF_DONE(status);
   if (!(i < ctl->ok)) return;
   V accv = V(0);
-  GRID_LOOP(c, A.n) {
-    V sv = stencil_row_t<V, C>(A, p, c);
+  ROW_LOOP(A, c, cx, cy, cz) {
+    V sv = stencil_row_t<V, C>(A, p, c, cx, cy, cz);
     s[c] = sv;
     accv += sv * p[c];
   }
@@ -225,14 +231,14 @@ __global__ void __launch_bounds__(kThreads) cheb_sweep_kernel(StencilT<V, C> A, 
                                                               double* __restrict__ out,
                                                               const int* __restrict__ status) {
   SKIP_IF_DONE(status);
-  GRID_LOOP(c, A.n) {
+  ROW_LOOP(A, c, i, j2, k) {
     const V dc = dj[c];
     const V xv = (j == 0 ? V(0) : x[c]) + dc;
     if (last) {
       out[c] = add ? add[c] + (double)xv : (double)xv;
     } else {
       x[c] = xv;
-      const V rv = r[c] - stencil_row_t<V, C>(A, dj, c);
+      const V rv = r[c] - stencil_row_t<V, C>(A, dj, c, i, j2, k);
       r[c] = rv;
       dn[c] = c1 * dc + c2 * (cv<V, C>(A.dinv[c]) * rv);
     }

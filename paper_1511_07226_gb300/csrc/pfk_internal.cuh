@@ -20,7 +20,8 @@
 namespace pfk {
 
 constexpr int kThreads = 256;          // threads per block of the streaming kernels
-constexpr int kMaxDots = PFK_MAX_MMAX + 8;
+constexpr int kMaxBlocksPerSm = 8;     // upper bound of every reduction kernel's grid, per SM
+constexpr int kPartialStride = PFK_MAX_MMAX + 8;   // upper bound of values per block in a reduction
 
 // Status codes kept in SolveCtl::status.
 enum DevStatus : int {
@@ -167,24 +168,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-level partial sums of `nd` accumulators, written to
-// partials[blockIdx.x * stride + j]; then the last block to arrive combines all
-// blocks' partials in a fixed order (lane-strided over blocks, then a fixed
-// shuffle tree) into sums[j] (shared memory of the last block).
-// Returns true in the last block (all its threads).  `smem` must hold
-// (kThreads / 32) * nd doubles; sums must hold nd doubles.
-template <int ND>
-__device__ __forceinline__ bool reduce_last_block(const double (&acc)[ND], int nd, double* partials, int stride,
-                                                  unsigned int* counter, double* smem, double* sums) {
+// Second half of reduce_last_block, for kernels that prepare the per-warp
+// partial sums themselves: smem[w * nd + j] holds warp w's sum of value j.
+// Writes this block's partial sums, then the last block to arrive combines all
+// blocks' partials in a fixed order into sums[j] and returns true.
+__device__ __forceinline__ bool combine_block_partials(const double* smem, int nd, double* partials, int stride,
+                                                       unsigned int* counter, double* sums) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-#pragma unroll
-  for (int j = 0; j < ND; ++j) {
-    if (j < nd) {
-      double v = warp_sum(acc[j]);
-      if (lane == 0) smem[warp * nd + j] = v;
-    }
-  }
-  __syncthreads();
   for (int j = threadIdx.x; j < nd; j += blockDim.x) {
     double v = 0.0;
     for (int w = 0; w < nwarps; ++w) v += smem[w * nd + j];
@@ -210,6 +200,27 @@ __device__ __forceinline__ bool reduce_last_block(const double (&acc)[ND], int n
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
   return true;
+}
+
+// Block-level partial sums of `nd` accumulators, written to
+// partials[blockIdx.x * stride + j]; then the last block to arrive combines all
+// blocks' partials in a fixed order (lane-strided over blocks, then a fixed
+// shuffle tree) into sums[j] (shared memory of the last block).
+// Returns true in the last block (all its threads).  `smem` must hold
+// (kThreads / 32) * nd doubles; sums must hold nd doubles.
+template <int ND>
+__device__ __forceinline__ bool reduce_last_block(const double (&acc)[ND], int nd, double* partials, int stride,
+                                                  unsigned int* counter, double* smem, double* sums) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    if (j < nd) {
+      double v = warp_sum(acc[j]);
+      if (lane == 0) smem[warp * nd + j] = v;
+    }
+  }
+  __syncthreads();
+  return combine_block_partials(smem, nd, partials, stride, counter, sums);
 }
 
 // ---------------------------------------------------------------------------

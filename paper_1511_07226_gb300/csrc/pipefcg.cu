@@ -10,7 +10,8 @@
 //       - advances x_i, r_i, u_i (= tilde-u_i), w_i with alpha_{i-1},
 //       - accumulates the partial sums of gamma_i = <u_i, r_i>,
 //         delta_i = <u_i, w_i>, ||r_i||^2 and <u_i, s_k> for every s_k of
-//         W_{i-1} and s_{i-1} (the s_k are still in registers from the MAXPY),
+//         W_{i-1} and s_{i-1} (the s_k read by the MAXPY are kept on chip, so
+//         the window is read from HBM once),
 //       - writes the preconditioner input t = w_i - r_i (eq. BwMinusR),
 //       - and, in the last block to finish, combines the partial sums in a fixed
 //         order and computes beta_{i,k} = -<u_i, s_k>/eta_k,
@@ -62,15 +63,32 @@ __device__ __forceinline__ void push_history(SolveCtl* c, double rho, double rn,
   c->hist_len += 1;
 }
 
+// Threads per block of the fused pass and resident blocks per SM (24 warps per
+// SM).  Each thread handles one element per tile.  The history values s_k
+// read by the MAXPYs are parked in shared memory, one row per window slot and
+// one column per thread, and after the advance each warp computes the window
+// dot products transposed: lane j sums u_e s_{k_j,e} over the warp's 32
+// elements e.  So every thread holds one window accumulator instead of nu, the
+// FP64 instruction count is unchanged, and register use stays low.
+constexpr int kPassThreads = 128;
+constexpr int kPassBlocksPerSm = 6;
+constexpr int kSkStride = kPassThreads + 1;   // padding: conflict-free row reads
+static_assert(kPassBlocksPerSm <= kMaxBlocksPerSm, "partials are sized for kMaxBlocksPerSm blocks per SM");
+static_assert(PFK_MAX_MMAX + 4 <= kPartialStride, "partials are sized for kPartialStride values per block");
+
 template <int NW>
-__global__ void __launch_bounds__(kThreads, 1) pipefcg_pass(FcgArgs a) {
+__global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(FcgArgs a) {
   SolveCtl* ctl = a.ctl;
   if (ctl->status != kRun) return;
   constexpr int ND = NW + 4;
+  constexpr int NWARPS = kPassThreads / 32;
   __shared__ double s_beta[NW];
   __shared__ size_t s_off[NW];
-  __shared__ double s_red[(kThreads / 32) * ND];
+  __shared__ double s_red[NWARPS * ND];
   __shared__ double s_sum[ND];
+  __shared__ double s_sk[NW * kSkStride];
+  __shared__ double s_u[kPassThreads];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int iprev = ctl->i;      // i - 1
   const int nwp = ctl->nw;       // |W_{i-1}|
   const double alpha = ctl->alpha;
@@ -83,51 +101,79 @@ __global__ void __launch_bounds__(kThreads, 1) pipefcg_pass(FcgArgs a) {
   }
   __syncthreads();
   const size_t coff = (size_t)(iprev % slots) * (size_t)N;
+  double* my_sk = s_sk + threadIdx.x;
+  const double* warp_u = s_u + warp * 32;
+  const double* lane_row = s_sk + lane * kSkStride + warp * 32;
 
-  double acc[ND];
-#pragma unroll
-  for (int j = 0; j < ND; ++j) acc[j] = 0.0;
+  // per-thread sums of gamma, delta, ||r||^2, <u, s_{i-1}>; lane-owned window sum
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0, gw = 0.0;
 
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    const double u0 = a.u[e], w0 = a.w[e];
-    double p = u0, s = w0, q = a.m[e], z = a.n[e];
-    double sk[NW];
+  for (int64_t base = (int64_t)blockIdx.x * kPassThreads; base < N; base += (int64_t)gridDim.x * kPassThreads) {
+    const int64_t e = base + threadIdx.x;
+    double un = 0.0;
+    if (e < N) {
+      const double u0 = a.u[e], w0 = a.w[e];
+      double p = u0, s = w0, q = a.m[e], z = a.n[e];
 #pragma unroll
-    for (int j = 0; j < NW; ++j) {
-      if (j < nwp) {
-        const size_t o = s_off[j] + e;
-        const double b = s_beta[j];
-        const double sv = a.S[o];
-        p = fma(b, a.P[o], p);
-        s = fma(b, sv, s);
-        q = fma(b, a.Q[o], q);
-        z = fma(b, a.Z[o], z);
-        sk[j] = sv;
+      for (int j = 0; j < NW; ++j) {
+        if (j < nwp) {
+          const size_t o = s_off[j] + e;
+          const double b = s_beta[j];
+          const double sv = a.S[o];
+          p = fma(b, a.P[o], p);
+          s = fma(b, sv, s);
+          q = fma(b, a.Q[o], q);
+          z = fma(b, a.Z[o], z);
+          my_sk[j * kSkStride] = sv;
+        }
       }
-    }
-    a.P[coff + e] = p;
-    a.S[coff + e] = s;
-    a.Q[coff + e] = q;
-    a.Z[coff + e] = z;
-    const double xn = fma(alpha, p, a.x[e]);
-    const double rn = fma(-alpha, s, a.r[e]);
-    const double un = fma(-alpha, q, u0);
-    const double wn = fma(-alpha, z, w0);
-    a.x[e] = xn;
-    a.r[e] = rn;
-    a.u[e] = un;
-    a.w[e] = wn;
-    if (!a.naive) a.t[e] = wn - rn;
-    acc[0] = fma(un, rn, acc[0]);
-    acc[1] = fma(un, wn, acc[1]);
-    acc[2] = fma(rn, rn, acc[2]);
-    acc[3] = fma(un, s, acc[3]);
+      a.P[coff + e] = p;
+      a.S[coff + e] = s;
+      a.Q[coff + e] = q;
+      a.Z[coff + e] = z;
+      const double xn = fma(alpha, p, a.x[e]);
+      const double rn = fma(-alpha, s, a.r[e]);
+      un = fma(-alpha, q, u0);
+      const double wn = fma(-alpha, z, w0);
+      a.x[e] = xn;
+      a.r[e] = rn;
+      a.u[e] = un;
+      a.w[e] = wn;
+      if (!a.naive) a.t[e] = wn - rn;
+      g0 = fma(un, rn, g0);
+      g1 = fma(un, wn, g1);
+      g2 = fma(rn, rn, g2);
+      g3 = fma(un, s, g3);
+    } else {
 #pragma unroll
-    for (int j = 0; j < NW; ++j)
-      if (j < nwp) acc[4 + j] = fma(un, sk[j], acc[4 + j]);
+      for (int j = 0; j < NW; ++j)
+        if (j < nwp) my_sk[j * kSkStride] = 0.0;
+    }
+    s_u[threadIdx.x] = un;
+    __syncwarp();
+    if (lane < nwp) {
+      double c = gw;
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) c = fma(warp_u[t], lane_row[t], c);
+      gw = c;
+    }
+    __syncwarp();
   }
 
-  if (!reduce_last_block<ND>(acc, nwp + 4, a.partials, ND, &ctl->counter, s_red, s_sum)) return;
+  // block partials: scalars by warp reduction, window sums straight from their lanes
+  {
+    const double w0 = warp_sum(g0), w1 = warp_sum(g1), w2 = warp_sum(g2), w3 = warp_sum(g3);
+    const int nd = nwp + 4;
+    if (lane == 0) {
+      s_red[warp * nd + 0] = w0;
+      s_red[warp * nd + 1] = w1;
+      s_red[warp * nd + 2] = w2;
+      s_red[warp * nd + 3] = w3;
+    }
+    if (lane < nwp) s_red[warp * nd + 4 + lane] = gw;
+    __syncthreads();
+  }
+  if (!combine_block_partials(s_red, nwp + 4, a.partials, ND, &ctl->counter, s_sum)) return;
   if (threadIdx.x != 0) return;
 
   // ---- scalar phase of iteration i (one thread) ----
@@ -220,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) pipefcg_fill_dots(const double* __re
 
 template <int NW>
 static cudaError_t launch_pass(const FcgArgs& a, int blocks, cudaStream_t st) {
-  pipefcg_pass<NW><<<blocks, kThreads, 0, st>>>(a);
+  pipefcg_pass<NW><<<blocks, kPassThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -267,7 +313,9 @@ class PipeFcg : public Method {
     if ((e = op_apply(env.op, u_, w_, nullptr, nullptr, st)) != cudaSuccess) return e;  // w_0 = A p_0, p_0 = u_0
     if ((e = env.pc_apply(w_, m_, nullptr, nullptr)) != cudaSuccess) return e;           // m_0 = B(w_0)
     if ((e = op_apply(env.op, m_, n_, nullptr, nullptr, st)) != cudaSuccess) return e;   // n_0 = A m_0
-    pipefcg_fill_dots<<<stream_blocks(env.ctx, N_, 2), kThreads, 0, st>>>(u_, r_, w_, N_, env.ctl, env.partials);
+    const int blocks = stream_blocks(env.ctx, N_, 2);
+    if (!env.partials_fit(blocks, 3)) return cudaErrorInvalidValue;
+    pipefcg_fill_dots<<<blocks, kThreads, 0, st>>>(u_, r_, w_, N_, env.ctl, env.partials);
     return cudaGetLastError();
   }
 
@@ -280,7 +328,11 @@ class PipeFcg : public Method {
     const int tmpl = pipefcg_template(mmax_);
     cudaError_t e = env.mark_pass(0);
     if (e != cudaSuccess) return e;
-    e = launch_pass_any(a, tmpl, stream_blocks(env.ctx, N_, 1), env.st);
+    const int64_t need = (N_ + kPassThreads - 1) / kPassThreads;
+    const int64_t cap = (int64_t)env.ctx->num_sms * kPassBlocksPerSm;
+    const int blocks = (int)(need < cap ? need : cap);
+    if (!env.partials_fit(blocks, tmpl + 4)) return cudaErrorInvalidValue;
+    e = launch_pass_any(a, tmpl, blocks, env.st);
     if (e != cudaSuccess) return e;
     if ((e = env.mark_pass(1)) != cudaSuccess) return e;
     const int* status = &env.ctl->status;

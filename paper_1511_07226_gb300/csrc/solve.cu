@@ -123,14 +123,16 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
     set_error(ctx, "method not available");
     return PFK_ERR_INVALID;
   }
-  // ---- workspace: control block | method vectors | partials | history ----
-  const int blocks = stream_blocks(ctx, N, 2);
+  // ---- workspace: control block | method vectors | partials | scalars | history ----
+  // partials: room for any kernel of the solve (at most kMaxBlocksPerSm blocks
+  // per SM, at most kPartialStride values per block); launches check it.
   const int64_t wd = M->workspace_doubles(N, mmax);
-  const int64_t pd = (int64_t)blocks * (PFK_MAX_MMAX + 8) * 2 + 64;
+  const int64_t pd = (int64_t)ctx->num_sms * kMaxBlocksPerSm * kPartialStride;
+  const int64_t sd = 64;
   const int hist_cap = prm->history ? prm->history_capacity : 0;
   const int64_t hd = (int64_t)hist_cap * PFK_HISTORY_FIELDS;
   const size_t ctl_bytes = (sizeof(SolveCtl) + 255) / 256 * 256;
-  const size_t need = (size_t)(wd + pd + hd) * sizeof(double) + ctl_bytes + 256;
+  const size_t need = (size_t)(wd + pd + sd + hd) * sizeof(double) + ctl_bytes + 256;
   if (ctx->ws_bytes < need) {
     if (ctx->ws) cudaFreeAsync(ctx->ws, st);
     ctx->ws = nullptr;
@@ -147,8 +149,8 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
   SolveCtl* ctl = (SolveCtl*)base;
   double* ws = (double*)(base + ctl_bytes);
   double* partials = ws + wd;
-  double* hist = hist_cap ? partials + pd : nullptr;
-  double* d_out = partials + pd - 8;
+  double* d_out = partials + pd;
+  double* hist = hist_cap ? d_out + sd : nullptr;
   M->bind(ws, N, mmax);
 
   SolveCtl h;
@@ -171,6 +173,7 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
   env.st = st;
   env.ctl = ctl;
   env.partials = partials;
+  env.partials_cap = pd;
   env.N = N;
   env.pass_ev0 = env.pass_ev1 = nullptr;
 

@@ -13,7 +13,11 @@ struct SolveEnv {
   cudaStream_t st;
   SolveCtl* ctl;             // device control block
   double* partials;          // reduction partials of the method's kernels
+  int64_t partials_cap;      // doubles available at `partials`
   int64_t N;
+
+  // True if a launch of `blocks` blocks writing `stride` partials each fits.
+  bool partials_fit(int blocks, int stride) const { return (int64_t)blocks * stride <= partials_cap; }
   cudaEvent_t pass_ev0, pass_ev1;   // profiling: recorded around the fused pass (or null)
 
   // out = add + B(v); B = identity when pc is null.
