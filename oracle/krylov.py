@@ -66,6 +66,8 @@ class Result:
     restarts: int = 0
     breakdowns: int = 0
     replacements: int = 0
+    cycles: int = 0              # GMRES-type restart cycles (not counted in restarts)
+    sigma: float = float("nan")  # shift used by CGFGMRES / PIPEFGMRES
     rho0: float = float("nan")
     rnorm_true: float = float("nan")
     bnorm: float = float("nan")
@@ -616,7 +618,21 @@ def fgmres(A, B, b, x0, prm: Params) -> Result:
             return mon.finish(x, "maxit")
         if done == "converged" and mon.accept(x):
             return mon.finish(x, "converged")
-        res.restarts += 0 if done == "converged" else 1
+        res.cycles += 1
+
+
+def estimate_sigma(A, B, b, iters: int = 10) -> float:
+    """Shift for CGFGMRES / PIPEFGMRES when none is given: an estimate of the
+    largest eigenvalue of the preconditioned operator (Sec. 5.3), by power
+    iteration on v -> A B(v) from v = b / ||b||; returns ||A B(v)|| of the last
+    step (||v|| = 1)."""
+    v = np.asarray(b, dtype=np.float64) / np.linalg.norm(b)
+    nrm = 0.0
+    for _ in range(iters):
+        y = A(B(v))
+        nrm = float(np.linalg.norm(y))
+        v = y / nrm
+    return nrm
 
 
 def _fgmres_single_reduction(A, B, b, x0, prm: Params, pipelined: bool) -> Result:
@@ -624,7 +640,8 @@ def _fgmres_single_reduction(A, B, b, x0, prm: Params, pipelined: bool) -> Resul
     mon = _Monitor(A, b, prm, res)
     x = np.array(x0, dtype=np.float64)
     m = prm.mmax
-    sigma = prm.sigma
+    sigma = prm.sigma if not np.isnan(prm.sigma) else estimate_sigma(A, B, b)
+    res.sigma = sigma
     after_bd = False
     while True:
         r0 = b - A(x)
@@ -703,8 +720,7 @@ def _fgmres_single_reduction(A, B, b, x0, prm: Params, pipelined: bool) -> Resul
         after_bd = False
         if status == "converged" and mon.accept(x):
             return mon.finish(x, "converged")
-        if status != "converged":
-            res.restarts += 1
+        res.cycles += 1
 
 
 def cgfgmres(A, B, b, x0, prm: Params) -> Result:

@@ -1,0 +1,329 @@
+// PIPEGCR (Alg. 11) on one GPU.
+//
+// Iteration i is three kernel groups reading their scalars from the device
+// control block (capturable in one CUDA graph):
+//
+//  1. pipegcr_advance<NW>: the deferred MAXPYs of iteration i-1
+//       p_{i-1} = u_{i-1} + sum beta_{i-1,k} p_k,  s_{i-1} = w_{i-1} + ...,
+//       q_{i-1} = m_{i-1} + ...
+//     into ring slot (i-1) mod (mmax+1), then x_i, r_i and u_i (tilde-u) with
+//     alpha_{i-1};
+//  2. pipegcr_apply_dots<NW>: w_i = A u_i (stencil or CSR) fused with the
+//     single reduction of the iteration: gamma_i = <r_i, w_i>, delta_i =
+//     <w_i, w_i>, ||r_i||^2 and <w_i, s_k> for the nu_i stored s_k; writes the
+//     preconditioner input t = w_i - r_i; the last block computes beta, eta_i,
+//     alpha_i and the status;
+//  3. the preconditioner, m_i = u_i + B(w_i - r_i).
+//
+// Unlike Alg. 8 the operator product w_i = A u_i is explicit, so the
+// reduction overlaps only the preconditioner (Sec. 4.2).
+#include "pfk_internal.cuh"
+#include "solver.cuh"
+
+namespace pfk {
+
+struct GcrArgs {
+  double* x;
+  double* r;
+  double* u;
+  double* w;
+  const double* m;
+  double* t;
+  double* P;
+  double* S;
+  double* Q;
+  int64_t N;
+  int mmax;
+  SolveCtl* ctl;
+  double* partials;
+};
+
+constexpr int kGcrThreads = 128;
+constexpr int kGcrBlocksPerSm = 6;
+constexpr int kGcrStride = kGcrThreads + 1;
+static_assert(kGcrBlocksPerSm <= kMaxBlocksPerSm, "partials are sized for kMaxBlocksPerSm blocks per SM");
+
+template <int NW>
+__global__ void __launch_bounds__(kThreads, 3) pipegcr_advance(GcrArgs a) {
+  SolveCtl* ctl = a.ctl;
+  if (ctl->status != kRun) return;
+  __shared__ double s_beta[NW];
+  __shared__ size_t s_off[NW];
+  const int iprev = ctl->i;
+  const int nwp = ctl->nw;
+  const double alpha = ctl->alpha;
+  const int slots = a.mmax + 1;
+  const int64_t N = a.N;
+  if (threadIdx.x < nwp) {
+    const int k = iprev - nwp + (int)threadIdx.x;
+    s_beta[threadIdx.x] = ctl->beta[threadIdx.x];
+    s_off[threadIdx.x] = (size_t)(k % slots) * (size_t)N;
+  }
+  __syncthreads();
+  const size_t coff = (size_t)(iprev % slots) * (size_t)N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const double u0 = a.u[e];
+    double p = u0, s = a.w[e], q = a.m[e];
+#pragma unroll 4
+    for (int j = 0; j < nwp; ++j) {
+      const size_t o = s_off[j] + e;
+      const double b = s_beta[j];
+      p = fma(b, a.P[o], p);
+      s = fma(b, a.S[o], s);
+      q = fma(b, a.Q[o], q);
+    }
+    a.P[coff + e] = p;
+    a.S[coff + e] = s;
+    a.Q[coff + e] = q;
+    a.x[e] = fma(alpha, p, a.x[e]);
+    a.r[e] = fma(-alpha, s, a.r[e]);
+    a.u[e] = fma(-alpha, q, u0);
+  }
+}
+
+// Operator row value (A u)_c for the stencil (row-chunk mapping) or CSR.
+struct OpView {
+  // stencil
+  const double* d;
+  const double* kx;
+  const double* ky;
+  const double* kz;
+  int nx, ny, nz, ndim;
+  double a0, a1, a2;
+  int u0, u1, u2;
+  // CSR
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const double* vals;
+};
+
+__device__ __forceinline__ double op_row_stencil(const OpView& A, const double* __restrict__ m, int64_t c, int i,
+                                                 int j, int k) {
+  const int64_t sxy = (int64_t)A.nx * A.ny;
+  double acc = A.d[c] * m[c];
+  if (i > 0) acc = fma(-(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)), m[c - 1], acc);
+  if (i < A.nx - 1) acc = fma(-(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)), m[c + 1], acc);
+  if (j > 0) acc = fma(-(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)), m[c - A.nx], acc);
+  if (j < A.ny - 1) acc = fma(-(A.ky[c] + (A.u1 == 1 ? A.a1 : 0.0)), m[c + A.nx], acc);
+  if (A.ndim == 3) {
+    if (k > 0) acc = fma(-(A.kz[c - sxy] + (A.u2 == -1 ? A.a2 : 0.0)), m[c - sxy], acc);
+    if (k < A.nz - 1) acc = fma(-(A.kz[c] + (A.u2 == 1 ? A.a2 : 0.0)), m[c + sxy], acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ double op_row_csr(const OpView& A, const double* __restrict__ m, int64_t r) {
+  double acc = 0.0;
+  for (int32_t p = A.rowptr[r]; p < A.rowptr[r + 1]; ++p) acc = fma(A.vals[p], m[A.colidx[p]], acc);
+  return acc;
+}
+
+// Warps walk "chunks" of 32 consecutive unknowns: for a stencil, 32 cells of
+// one x-row (the row gives j, k); for CSR, 32 consecutive rows.  Each chunk's
+// w values and stored s_k values are staged in shared memory and lane jj of
+// the warp sums w_e s_{k_jj,e} over the chunk (the same transposed window dot
+// as in the PIPEFCG pass).
+template <int NW, bool STENCIL>
+__global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_dots(GcrArgs a, OpView A) {
+  SolveCtl* ctl = a.ctl;
+  if (ctl->status != kRun) return;
+  constexpr int ND = NW + 3;
+  constexpr int NWARPS = kGcrThreads / 32;
+  __shared__ size_t s_off[NW];
+  __shared__ double s_sk[NW * kGcrStride];
+  __shared__ double s_w[kGcrThreads];
+  __shared__ double s_red[NWARPS * ND];
+  __shared__ double s_sum[ND];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = ctl->i + 1;
+  const int nu = nu_window(i, a.mmax, ctl->truncation);
+  const int slots = a.mmax + 1;
+  const int64_t N = a.N;
+  if (threadIdx.x < nu) {
+    const int k = i - nu + (int)threadIdx.x;
+    s_off[threadIdx.x] = (size_t)(k % slots) * (size_t)N;
+  }
+  __syncthreads();
+  double* my_sk = s_sk + threadIdx.x;
+  const double* warp_w = s_w + warp * 32;
+  const double* lane_row = s_sk + lane * kGcrStride + warp * 32;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0, gw = 0.0;
+
+  const int64_t cpr = STENCIL ? (A.nx + 31) / 32 : 1;                  // chunks per x-row
+  const int64_t nchunks = STENCIL ? cpr * A.ny * A.nz : (N + 31) / 32;
+  const int64_t gwarps = (int64_t)gridDim.x * NWARPS;
+  for (int64_t ch0 = (int64_t)blockIdx.x * NWARPS; ch0 < nchunks; ch0 += gwarps) {
+    // all warps of the block iterate together (block-uniform trip count)
+    const int64_t ch = ch0 + warp;
+    double wv = 0.0;
+    bool valid = false;
+    int64_t c = 0;
+    if (ch < nchunks) {
+      if (STENCIL) {
+        const int64_t row = ch / cpr;
+        const int ix = (int)(ch - row * cpr) * 32 + lane;
+        if (ix < A.nx) {
+          valid = true;
+          c = row * A.nx + ix;
+          const int irow = (int)row;
+          wv = op_row_stencil(A, a.u, c, ix, irow % A.ny, irow / A.ny);
+        }
+      } else {
+        c = ch * 32 + lane;
+        if (c < N) {
+          valid = true;
+          wv = op_row_csr(A, a.u, c);
+        }
+      }
+    }
+    if (valid) {
+      const double rv = a.r[c];
+      a.w[c] = wv;
+      a.t[c] = wv - rv;
+      g0 = fma(rv, wv, g0);
+      g1 = fma(wv, wv, g1);
+      g2 = fma(rv, rv, g2);
+#pragma unroll
+      for (int j = 0; j < NW; ++j)
+        if (j < nu) my_sk[j * kGcrStride] = a.S[s_off[j] + c];
+    } else {
+#pragma unroll
+      for (int j = 0; j < NW; ++j)
+        if (j < nu) my_sk[j * kGcrStride] = 0.0;
+    }
+    s_w[threadIdx.x] = valid ? wv : 0.0;
+    __syncwarp();
+    if (lane < nu) {
+      double cacc = gw;
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) cacc = fma(warp_w[t], lane_row[t], cacc);
+      gw = cacc;
+    }
+    __syncwarp();
+  }
+  {
+    const double w0 = warp_sum(g0), w1 = warp_sum(g1), w2 = warp_sum(g2);
+    const int nd = nu + 3;
+    if (lane == 0) {
+      s_red[warp * nd + 0] = w0;
+      s_red[warp * nd + 1] = w1;
+      s_red[warp * nd + 2] = w2;
+    }
+    if (lane < nu) s_red[warp * nd + 3 + lane] = gw;
+    __syncthreads();
+  }
+  if (!combine_block_partials(s_red, nu + 3, a.partials, ND, &ctl->counter, s_sum)) return;
+  if (threadIdx.x != 0) return;
+  // algorithmic traffic of the iteration's two kernels: advance reads u, w, m,
+  // x, r and 3 nu_{i-1} history vectors, writes p, s, q, x, r, u; the apply
+  // reads u, r, the operator (4 coefficient arrays for a stencil) and nu_i s_k,
+  // writes w and t.  FP64: 3 nu_{i-1} + 3 + 7 (stencil) + nu_i + 3 FMAs, 1 sub.
+  const int nwp = ctl->nw;
+  ctl->passes += 1;
+  ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + (STENCIL ? 4 : 0) + nu + 2));
+  ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + (STENCIL ? 7 : 0) + nu + 3) + 1.0);
+  cgcr_iteration_scalars(ctl, i, nu, s_sum[0], s_sum[1], s_sum[2], s_sum + 3);
+}
+
+// Fill: gamma_0 = <r_0, w_0> with w_0 = A u_0 = s_0, eta_0 = <s_0, s_0>, ||r_0||^2.
+__global__ void __launch_bounds__(kThreads) pipegcr_fill_dots(const double* __restrict__ r,
+                                                              const double* __restrict__ w, int64_t N,
+                                                              SolveCtl* ctl, double* partials) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const double rv = r[e], wv = w[e];
+    acc[0] = fma(rv, wv, acc[0]);
+    acc[1] = fma(wv, wv, acc[1]);
+    acc[2] = fma(rv, rv, acc[2]);
+  }
+  __shared__ double s_red[(kThreads / 32) * 3];
+  __shared__ double s_sum[3];
+  if (!reduce_last_block<3>(acc, 3, partials, 3, &ctl->counter, s_red, s_sum)) return;
+  if (threadIdx.x != 0) return;
+  cgcr_fill_scalars(ctl, s_sum[0], s_sum[1], s_sum[2]);
+}
+
+static int gcr_template(int mmax) { return mmax <= 8 ? 8 : mmax <= 16 ? 16 : 32; }
+
+class PipeGcr : public Method {
+ public:
+  int64_t workspace_doubles(int64_t N, int mmax) const override { return 6 * N + 3 * (int64_t)(mmax + 1) * N; }
+
+  void bind(double* ws, int64_t N, int mmax) override {
+    N_ = N;
+    mmax_ = mmax;
+    r_ = ws; u_ = r_ + N; w_ = u_ + N; m_ = w_ + N; t_ = m_ + N; tmp_ = t_ + N;
+    P_ = tmp_ + N;
+    S_ = P_ + (mmax + 1) * N;
+    Q_ = S_ + (mmax + 1) * N;
+  }
+
+  double* scratch() override { return tmp_; }
+
+  cudaError_t fill(const SolveEnv& env, const double* b, double* x) override {
+    cudaStream_t st = env.st;
+    cudaError_t e;
+    if ((e = op_apply(env.op, x, r_, b, nullptr, st)) != cudaSuccess) return e;          // r_0 = b - A x_0
+    if ((e = env.pc_apply(r_, u_, nullptr, nullptr)) != cudaSuccess) return e;           // u_0 = B(r_0), p_0 = u_0
+    if ((e = op_apply(env.op, u_, w_, nullptr, nullptr, st)) != cudaSuccess) return e;  // s_0 = A p_0 (kept as w)
+    if ((e = env.pc_apply(w_, m_, nullptr, nullptr)) != cudaSuccess) return e;           // q_0 = B(s_0) (kept as m)
+    const int blocks = stream_blocks(env.ctx, N_, 2);
+    if (!env.partials_fit(blocks, 3)) return cudaErrorInvalidValue;
+    pipegcr_fill_dots<<<blocks, kThreads, 0, st>>>(r_, w_, N_, env.ctl, env.partials);
+    return cudaGetLastError();
+  }
+
+  cudaError_t iteration(const SolveEnv& env, double* x) override {
+    GcrArgs a;
+    a.x = x; a.r = r_; a.u = u_; a.w = w_; a.m = m_; a.t = t_;
+    a.P = P_; a.S = S_; a.Q = Q_;
+    a.N = N_; a.mmax = mmax_; a.ctl = env.ctl; a.partials = env.partials;
+    const pfk_operator* op = env.op;
+    OpView A;
+    A.d = op->d; A.kx = op->kx; A.ky = op->ky; A.kz = op->kz;
+    A.nx = op->nx; A.ny = op->ny; A.nz = op->nz; A.ndim = op->ndim;
+    A.a0 = op->adv[0]; A.a1 = op->adv[1]; A.a2 = op->adv[2];
+    A.u0 = op->upw[0]; A.u1 = op->upw[1]; A.u2 = op->upw[2];
+    A.rowptr = op->rowptr; A.colidx = op->colidx; A.vals = op->vals;
+    const bool stencil = op->rowptr == nullptr;
+    const int tmpl = gcr_template(mmax_);
+    const int ablocks = stream_blocks(env.ctx, N_, 4);
+    const int64_t chunks = stencil ? (int64_t)((op->nx + 31) / 32) * op->ny * op->nz : (N_ + 31) / 32;
+    const int64_t need = (chunks + kGcrThreads / 32 - 1) / (kGcrThreads / 32);
+    const int64_t cap = (int64_t)env.ctx->num_sms * kGcrBlocksPerSm;
+    const int dblocks = (int)(need < cap ? need : cap);
+    if (!env.partials_fit(dblocks, tmpl + 3)) return cudaErrorInvalidValue;
+    cudaError_t e = env.mark_pass(0);
+    if (e != cudaSuccess) return e;
+    switch (tmpl) {
+      case 8:
+        pipegcr_advance<8><<<ablocks, kThreads, 0, env.st>>>(a);
+        if (stencil) pipegcr_apply_dots<8, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        else pipegcr_apply_dots<8, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        break;
+      case 16:
+        pipegcr_advance<16><<<ablocks, kThreads, 0, env.st>>>(a);
+        if (stencil) pipegcr_apply_dots<16, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        else pipegcr_apply_dots<16, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        break;
+      default:
+        pipegcr_advance<32><<<ablocks, kThreads, 0, env.st>>>(a);
+        if (stencil) pipegcr_apply_dots<32, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        else pipegcr_apply_dots<32, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = env.mark_pass(1)) != cudaSuccess) return e;
+    return env.pc_apply(t_, m_, u_, &env.ctl->status);   // m_i = B(w_i - r_i) + u_i
+  }
+
+ private:
+  int64_t N_ = 0;
+  int mmax_ = 0;
+  double *r_ = nullptr, *u_ = nullptr, *w_ = nullptr, *m_ = nullptr, *t_ = nullptr, *tmp_ = nullptr;
+  double *P_ = nullptr, *S_ = nullptr, *Q_ = nullptr;
+};
+
+Method* make_pipegcr() { return new PipeGcr(); }
+
+}  // namespace pfk

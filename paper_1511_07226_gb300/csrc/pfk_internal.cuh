@@ -31,6 +31,7 @@ enum DevStatus : int {
   kMaxit = 3,
   kFillBreakdown = 4,   // eta_0 <= 0 in a pipeline fill
   kNonFinite = 5,
+  kCycleEnd = 6,        // GMRES types: restart length reached
 };
 
 // Device control block of one solve.

@@ -51,18 +51,6 @@ struct FcgArgs {
   double* partials;
 };
 
-__device__ __forceinline__ int nu_window(int i, int mmax, int truncation) {
-  return truncation == PFK_TRUNC_RESTART ? ((i - 1) % mmax) + 1 : (i < mmax ? i : mmax);
-}
-
-__device__ __forceinline__ void push_history(SolveCtl* c, double rho, double rn, double eta, double alpha) {
-  if (c->history && c->hist_len < c->hist_cap) {
-    double* h = c->history + (size_t)c->hist_len * PFK_HISTORY_FIELDS;
-    h[0] = rho; h[1] = rn; h[2] = eta; h[3] = alpha;
-  }
-  c->hist_len += 1;
-}
-
 // Threads per block of the fused pass and resident blocks per SM (24 warps per
 // SM).  Each thread handles one element per tile.  The history values s_k
 // read by the MAXPYs are parked in shared memory, one row per window slot and
@@ -185,41 +173,12 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
   ctl->passes += 1;
   ctl->alg_bytes += 8.0 * (double)N * (double)(4 * nwp + 14 + (a.naive ? 0 : 1));
   ctl->alg_flops += (double)N * (2.0 * (5 * nwp + 8) + (a.naive ? 0.0 : 1.0));
-  ctl->it += 1;
-  ctl->i = i;
-  ctl->gamma = gamma;
-  ctl->delta = delta;
-  const double rnorm = sqrt(rr);
-  const double rho = ctl->norm == PFK_NORM_NATURAL ? sqrt(fabs(gamma)) : rnorm;
-  ctl->rho = rho;
-  const int hslot = ctl->hist_len;
-  push_history(ctl, rho, rnorm, nan(""), nan(""));
-  if (!isfinite(rho)) { ctl->status = kNonFinite; return; }
-  if (rho <= ctl->target) { ctl->status = kConverged; return; }
   const int nu = nu_window(i, a.mmax, ctl->truncation);
-  const int off = nwp + 1 - nu;     // position of k = i - nu among (W_{i-1}, i-1)
-  double sumb = 0.0;
-  for (int jj = 0; jj < nu; ++jj) {
-    const int src = off + jj;        // 0..nwp-1: W_{i-1}; nwp: s_{i-1}
-    const double c = src < nwp ? s_sum[4 + src] : s_sum[3];
-    const int k = i - nu + jj;
-    const double ek = ctl->eta_ring[k % slots];
-    const double b = -c / ek;
-    ctl->beta[jj] = b;
-    sumb += b * b * ek;
-  }
-  const double eta = delta - sumb;
-  const double al = eta != 0.0 ? gamma / eta : nan("");
-  ctl->eta = eta;
-  ctl->alpha = al;
-  ctl->nw = nu;
-  ctl->eta_ring[i % slots] = eta;
-  if (ctl->history && hslot < ctl->hist_cap) {
-    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 2] = eta;
-    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 3] = al;
-  }
-  if (eta <= 0.0) { ctl->status = kBreakdown; return; }
-  if (ctl->it >= ctl->maxit) { ctl->status = kMaxit; return; }
+  // window dots in order k = i-1-nwp .. i-1 (W_{i-1}, then s_{i-1}); W_i is
+  // the last nu of them
+  double cw[PFK_MAX_MMAX + 1];
+  for (int src = 0; src <= nwp; ++src) cw[src] = src < nwp ? s_sum[4 + src] : s_sum[3];
+  cgcr_iteration_scalars(ctl, i, nu, gamma, delta, rr, cw + (nwp + 1 - nu));
 }
 
 // Pipeline fill dots: gamma_0 = <u_0, r_0>, delta_0 = <u_0, w_0>, ||r_0||^2,
@@ -239,29 +198,8 @@ __global__ void __launch_bounds__(kThreads) pipefcg_fill_dots(const double* __re
   __shared__ double s_sum[3];
   if (!reduce_last_block<3>(acc, 3, partials, 3, &ctl->counter, s_red, s_sum)) return;
   if (threadIdx.x != 0) return;
-  const double gamma = s_sum[0], delta = s_sum[1];
-  const double rnorm = sqrt(s_sum[2]);
-  const double rho = ctl->norm == PFK_NORM_NATURAL ? sqrt(fabs(gamma)) : rnorm;
-  if (!ctl->target_set) {
-    ctl->rho0 = rho;
-    ctl->target = fmax(ctl->rtol * rho, ctl->atol);
-    ctl->target_set = 1;
-  }
-  const double eta = delta;
-  const double al = eta != 0.0 ? gamma / eta : nan("");
-  push_history(ctl, rho, rnorm, eta, al);
-  ctl->rho = rho;
-  ctl->gamma = gamma;
-  ctl->delta = delta;
-  ctl->eta = eta;
-  ctl->alpha = al;
-  ctl->i = 0;
-  ctl->nw = 0;
-  ctl->eta_ring[0] = eta;
-  if (!isfinite(rho)) ctl->status = kNonFinite;
-  else if (rho <= ctl->target) ctl->status = kConverged;
-  else if (eta <= 0.0) ctl->status = kFillBreakdown;
-  else ctl->status = kRun;
+  // eta_0 = delta_0 (Alg. 8)
+  cgcr_fill_scalars(ctl, s_sum[0], s_sum[1], s_sum[2]);
 }
 
 template <int NW>

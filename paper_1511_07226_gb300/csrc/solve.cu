@@ -44,10 +44,12 @@ __global__ void ctl_restart_kernel(SolveCtl* ctl) {
   ctl->counter = 0u;
 }
 
-static Method* make_method(int method) {
+static Method* make_method(int method, double sigma = NAN) {
   switch (method) {
     case PFK_PIPEFCG: return make_pipefcg(false);
     case PFK_PIPEFCG_NAIVE: return make_pipefcg(true);
+    case PFK_PIPEGCR: return make_pipegcr();
+    case PFK_PIPEFGMRES: return make_pipefgmres(sigma);
     default: return nullptr;
   }
 }
@@ -118,7 +120,7 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
   cudaStream_t st = ctx->stream;
   const int64_t N = op->n;
   const int mmax = prm->mmax;
-  std::unique_ptr<Method> M(make_method(prm->method));
+  std::unique_ptr<Method> M(make_method(prm->method, prm->sigma));
   if (!M) {
     set_error(ctx, "method not available");
     return PFK_ERR_INVALID;
@@ -186,6 +188,9 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
   PFK_CUDA(ctx, cudaMemcpyAsync(&bnorm, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
   PFK_CUDA(ctx, cudaStreamSynchronize(st));
   bnorm = std::sqrt(bnorm);
+  double sigma_used = NAN;
+  PFK_CUDA(ctx, M->prepare(env, b, d_out, &sigma_used));
+  const bool gmres = M->cycle_length() > 0;
 
   // ---- graphs: recorded on the library's own stream (the caller's may be the
   // legacy default stream, which cannot be captured), launched on the caller's ----
@@ -307,6 +312,16 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
       PFK_CUDA(ctx, cudaMemcpyAsync(&hc[0], ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
       PFK_CUDA(ctx, cudaStreamSynchronize(st));
       if (status == kRun) status = hc[0].status;
+    }
+    // GMRES types: least-squares solve over the cycle's valid columns and
+    // x = x_0 + U y, whatever ended the cycle
+    if (gmres && status != kNonFinite) {
+      PFK_CUDA(ctx, M->end_cycle(env, x));
+      kernel_launches += 2;
+    }
+    if (status == kCycleEnd) {
+      prev_breakdown = false;
+      continue;
     }
 
     if (status == kConverged) {

@@ -44,8 +44,106 @@ class Method {
   virtual cudaError_t end_cycle(const SolveEnv& env, double* x) { (void)env; (void)x; return cudaSuccess; }
   // Number of ring/Hessenberg columns (GMRES types restart after this many).
   virtual int cycle_length() const { return 0; }
+  // Once per solve, before the graphs are captured (e.g. the PIPEFGMRES shift
+  // estimate); may synchronise.  `dscalar` is a device scalar slot; the method
+  // reports the shift it uses (NaN if none) in *host_sigma.
+  virtual cudaError_t prepare(const SolveEnv& env, const double* b, double* dscalar, double* host_sigma) {
+    (void)env; (void)b; (void)dscalar;
+    *host_sigma = NAN;
+    return cudaSuccess;
+  }
 };
 
 Method* make_pipefcg(bool naive);
+Method* make_pipegcr();
+Method* make_pipefgmres(double sigma);
+
+// ---------------------------------------------------------------------------
+// Scalar phase shared by the CG- and CR-type methods (runs in one thread of the
+// last block of the kernel that completed the iteration's reduction)
+// ---------------------------------------------------------------------------
+
+// Truncation (Sec. 5): standard nu_i = min(i, nu_max); restart-style
+// nu_i = ((i - 1) mod nu_max) + 1.
+__device__ __forceinline__ int nu_window(int i, int mmax, int truncation) {
+  return truncation == PFK_TRUNC_RESTART ? ((i - 1) % mmax) + 1 : (i < mmax ? i : mmax);
+}
+
+__device__ __forceinline__ void push_history(SolveCtl* c, double rho, double rn, double eta, double alpha) {
+  if (c->history && c->hist_len < c->hist_cap) {
+    double* h = c->history + (size_t)c->hist_len * PFK_HISTORY_FIELDS;
+    h[0] = rho; h[1] = rn; h[2] = eta; h[3] = alpha;
+  }
+  c->hist_len += 1;
+}
+
+__device__ __forceinline__ double cgcr_rho(const SolveCtl* ctl, double gamma, double rr) {
+  return ctl->norm == PFK_NORM_NATURAL ? sqrt(fabs(gamma)) : sqrt(rr);
+}
+
+// Pipeline fill: gamma_0, eta_0 (= delta_0 for Alg. 8, <s_0, s_0> for Alg. 11),
+// ||r_0||^2 -> rho_0, target, alpha_0 = gamma_0 / eta_0 and the fill status.
+__device__ __forceinline__ void cgcr_fill_scalars(SolveCtl* ctl, double gamma, double eta, double rr) {
+  const double rho = cgcr_rho(ctl, gamma, rr);
+  if (!ctl->target_set) {
+    ctl->rho0 = rho;
+    ctl->target = fmax(ctl->rtol * rho, ctl->atol);
+    ctl->target_set = 1;
+  }
+  const double al = eta != 0.0 ? gamma / eta : nan("");
+  push_history(ctl, rho, sqrt(rr), eta, al);
+  ctl->rho = rho;
+  ctl->gamma = gamma;
+  ctl->eta = eta;
+  ctl->alpha = al;
+  ctl->i = 0;
+  ctl->nw = 0;
+  ctl->eta_ring[0] = eta;
+  if (!isfinite(rho)) ctl->status = kNonFinite;
+  else if (rho <= ctl->target) ctl->status = kConverged;
+  else if (eta <= 0.0) ctl->status = kFillBreakdown;
+  else ctl->status = kRun;
+}
+
+// Iteration i once its reduction is complete: gamma_i, delta_i, ||r_i||^2 and
+// the window dots c[jj] = <v_i, s_k>, k = i - nu_i + jj (v = u for Alg. 8,
+// w for Alg. 11).  Convergence test first (as in the listings' order), then
+// beta_{i,k} = -c_k / eta_k, eta_i = delta_i - sum_k beta_{i,k}^2 eta_k (k
+// ascending), alpha_i = gamma_i / eta_i; eta_i <= 0 is a norm breakdown.
+__device__ __forceinline__ void cgcr_iteration_scalars(SolveCtl* ctl, int i, int nu, double gamma, double delta,
+                                                       double rr, const double* c) {
+  const int slots = ctl->mmax + 1;
+  ctl->it += 1;
+  ctl->i = i;
+  ctl->gamma = gamma;
+  ctl->delta = delta;
+  const double rnorm = sqrt(rr);
+  const double rho = cgcr_rho(ctl, gamma, rr);
+  ctl->rho = rho;
+  const int hslot = ctl->hist_len;
+  push_history(ctl, rho, rnorm, nan(""), nan(""));
+  if (!isfinite(rho)) { ctl->status = kNonFinite; return; }
+  if (rho <= ctl->target) { ctl->status = kConverged; return; }
+  double sumb = 0.0;
+  for (int jj = 0; jj < nu; ++jj) {
+    const int k = i - nu + jj;
+    const double ek = ctl->eta_ring[k % slots];
+    const double b = -c[jj] / ek;
+    ctl->beta[jj] = b;
+    sumb += b * b * ek;
+  }
+  const double eta = delta - sumb;
+  const double al = eta != 0.0 ? gamma / eta : nan("");
+  ctl->eta = eta;
+  ctl->alpha = al;
+  ctl->nw = nu;
+  ctl->eta_ring[i % slots] = eta;
+  if (ctl->history && hslot < ctl->hist_cap) {
+    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 2] = eta;
+    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 3] = al;
+  }
+  if (eta <= 0.0) { ctl->status = kBreakdown; return; }
+  if (ctl->it >= ctl->maxit) { ctl->status = kMaxit; return; }
+}
 
 }  // namespace pfk

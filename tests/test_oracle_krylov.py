@@ -318,3 +318,14 @@ def test_truncation_rules():
     assert [K.nu_window(i, prm) for i in range(1, 8)] == [1, 2, 3, 3, 3, 3, 3]
     prm = K.Params(mmax=3, truncation="restart")
     assert [K.nu_window(i, prm) for i in range(1, 8)] == [1, 2, 3, 1, 2, 3, 1]
+
+
+def test_sigma_estimate_approaches_largest_eigenvalue():
+    """Power iteration on A B: for a symmetric A with B = D^-1 the estimate tends to
+    the largest eigenvalue of A D^-1 (checked against numpy.linalg.eigvals)."""
+    op, b = _stencil_problem(item=18, contrast=1.0)
+    a = op.to_dense()
+    lam = np.abs(np.linalg.eigvals(a / np.diag(a)[None, :])).max()
+    est = K.estimate_sigma(op, PC.JacobiPC(op), b, iters=200)
+    assert abs(est - lam) <= 1e-3 * lam
+    assert K.estimate_sigma(op, PC.JacobiPC(op), b) <= lam * (1 + 1e-12)
