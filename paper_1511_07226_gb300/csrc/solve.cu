@@ -50,6 +50,9 @@ static Method* make_method(int method, double sigma = NAN) {
     case PFK_PIPEFCG_NAIVE: return make_pipefcg(true);
     case PFK_PIPEGCR: return make_pipegcr();
     case PFK_PIPEFGMRES: return make_pipefgmres(sigma);
+    case PFK_FCG: return make_fcg();
+    case PFK_GCR: return make_gcr();
+    case PFK_FGMRES: return make_fgmres();
     default: return nullptr;
   }
 }

@@ -57,6 +57,9 @@ class Method {
 Method* make_pipefcg(bool naive);
 Method* make_pipegcr();
 Method* make_pipefgmres(double sigma);
+Method* make_fcg();
+Method* make_gcr();
+Method* make_fgmres();
 
 // ---------------------------------------------------------------------------
 // Scalar phase shared by the CG- and CR-type methods (runs in one thread of the
