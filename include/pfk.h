@@ -287,6 +287,35 @@ pfk_status pfk_solve_workspace_bytes(int method, int mmax, int64_t n, int64_t* b
 pfk_status pfk_pc_workspace_bytes(const pfk_pc* pc, int64_t* bytes);
 
 /* ------------------------------------------------------------------------ */
+/* Batched solve: many independent systems in one persistent launch          */
+/* ------------------------------------------------------------------------ */
+
+/* Solves nsys independent systems A_j x_j = b_j with PIPEFCG (Alg. 8) in one
+ * persistent kernel launch: each thread block takes the next system from a
+ * work counter (largest first) and runs that system's whole solve - fill,
+ * iterations, restarts, true-residual check - with block-level reductions, so
+ * no block ever waits for another.  A system's result does not depend on the
+ * other systems of the batch (bit for bit).
+ *  - ops[j]: stencil operators (matrix-free storage), at most 2^31 - 1 cells.
+ *  - pc: kind NONE, JACOBI or INNER_PCG with precision FP64 or FP32; applied
+ *    per system (the same description for all).
+ *  - params: method must be PFK_PIPEFCG; mmax <= PFK_MAX_MMAX; graph_iters and
+ *    profile are ignored; history (if set) holds nsys consecutive blocks of
+ *    history_capacity entries, one block per system.
+ *  - b[j], x[j]: host (ptrs_on_device = 0) or device (1) pointers of length
+ *    n_j; x[j] holds x0 on entry and the solution on exit.
+ *  - infos: nsys entries (may be NULL); time_ms is the kernel time of the
+ *    whole batch; block_threads used is reported in pass_launches.
+ *  - block_threads: threads per block (multiple of 32, 64..512), or 0 to pick
+ *    it by timing a short trial of each candidate on this batch (cached for
+ *    batches of the same size profile in this context).
+ * Returns PFK_OK if every system converged, else the first non-OK status of a
+ * system (each system's own status is in infos[j].status). */
+pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* const* ops, const pfk_pc_desc* pc,
+                             const pfk_solve_params* params, const double* const* b, double* const* x,
+                             int ptrs_on_device, int block_threads, pfk_solve_info* infos);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free preconditioner application                                */
 /* ------------------------------------------------------------------------ */
 

@@ -106,6 +106,7 @@ pfk_status pfk_create_operator(pfk_context* ctx, const pfk_operator_desc* desc, 
   pfk_operator* op = new (std::nothrow) pfk_operator();
   if (!op) return PFK_ERR_OOM;
   op->ctx = ctx;
+  op->device = ctx->device;
   op->kind = desc->kind;
   op->storage = desc->storage;
   pfk_status s;
@@ -143,8 +144,10 @@ pfk_status pfk_create_operator(pfk_context* ctx, const pfk_operator_desc* desc, 
 
 pfk_status pfk_destroy_operator(pfk_operator* op) {
   if (!op) return PFK_OK;
-  cudaSetDevice(op->ctx->device);
-  cudaStreamSynchronize(op->ctx->stream);
+  // the operator may outlive its context (e.g. finalisation order in a
+  // garbage-collected binding): use the device recorded at creation only
+  cudaSetDevice(op->device);
+  cudaDeviceSynchronize();
   void* ptrs[] = {op->d, op->kx, op->ky, op->kz, op->dinv, op->d32, op->kx32, op->ky32, op->kz32, op->dinv32,
                   op->d16, op->kx16, op->ky16, op->kz16, op->dinv16, op->rowptr, op->colidx, op->vals,
                   op->csr_dinv};
@@ -176,6 +179,7 @@ pfk_status pfk_create_preconditioner(pfk_context* ctx, const pfk_operator* op, c
   cudaSetDevice(ctx->device);
   pfk_pc* pc = new (std::nothrow) pfk_pc();
   if (!pc) return PFK_ERR_OOM;
+  pc->device = ctx->device;
   pfk_status s = create_pc(ctx, op, desc, pc);
   if (s != PFK_OK) {
     pfk_destroy_preconditioner(pc);
@@ -187,10 +191,9 @@ pfk_status pfk_create_preconditioner(pfk_context* ctx, const pfk_operator* op, c
 
 pfk_status pfk_destroy_preconditioner(pfk_pc* pc) {
   if (!pc) return PFK_OK;
-  if (pc->ctx) {
-    cudaSetDevice(pc->ctx->device);
-    cudaStreamSynchronize(pc->ctx->stream);
-  }
+  // as for operators: never dereference the (possibly destroyed) context
+  cudaSetDevice(pc->device);
+  cudaDeviceSynchronize();
   if (pc->buf) cudaFree(pc->buf);
   if (pc->ctl) cudaFree(pc->ctl);
   if (pc->partials) cudaFree(pc->partials);

@@ -94,7 +94,8 @@ struct pfk_context {
 };
 
 struct pfk_operator {
-  pfk_context* ctx = nullptr;
+  pfk_context* ctx = nullptr;   // used while the context lives; destruction uses `device`
+  int device = 0;
   int kind = 0;
   int storage = 0;
   int nx = 0, ny = 0, nz = 0, ndim = 0;
@@ -128,7 +129,8 @@ struct pfk_operator {
 };
 
 struct pfk_pc {
-  pfk_context* ctx = nullptr;
+  pfk_context* ctx = nullptr;   // used while the context lives; destruction uses `device`
+  int device = 0;
   const pfk_operator* op = nullptr;
   int kind = 0;
   int inner = 0;

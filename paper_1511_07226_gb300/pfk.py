@@ -86,6 +86,9 @@ _SIGS = {
     "pfk_solve_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_int64)]),
     "pfk_pc_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "pfk_pc_apply_inner_pcg_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "pfk_solve_batched": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(PcDesc),
+                                    C.POINTER(SolveParams), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                    C.c_int, C.POINTER(SolveInfo)]),
 }
 
 
@@ -345,6 +348,41 @@ def pc_apply_inner_pcg_noalloc(ctx: Context, op: Operator, inner_iters: int, v, 
     _check(load().pfk_pc_apply_inner_pcg_noalloc(ctx.h, op.h, int(inner_iters), C.c_void_p(vd.data_ptr()),
                                                  C.c_void_p(y.data_ptr())), ctx.h)
     return y
+
+
+def solve_batched(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_iters=4, precision="fp64",
+                  history: int = 0, block_threads: int = 0, **kw):
+    """Solves independent systems ops[j] x_j = bs[j] in one persistent launch (PIPEFCG).
+
+    bs / x0s are NumPy arrays (host path).  Returns (xs, infos, histories)."""
+    lib = load()
+    nsys = len(ops)
+    prm = make_params(**kw)
+    hist = None
+    if history:
+        hist = np.full((nsys, history, HISTORY_FIELDS), np.nan)
+        prm.history = hist.ctypes.data
+        prm.history_capacity = history
+    d = PcDesc()
+    d.kind = PC_KINDS[pc_kind]
+    d.inner_iters = int(inner_iters)
+    d.precision = PRECISIONS[precision]
+    bh = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+    xs = [np.zeros_like(b) if x0s is None else np.array(x0s[j], dtype=np.float64, copy=True)
+          for j, b in enumerate(bh)]
+    oparr = (C.c_void_p * nsys)(*[op.h.value for op in ops])
+    barr = (C.c_void_p * nsys)(*[b.ctypes.data for b in bh])
+    xarr = (C.c_void_p * nsys)(*[x.ctypes.data for x in xs])
+    infos = (SolveInfo * nsys)()
+    st = lib.pfk_solve_batched(ctx.h, nsys, oparr, C.byref(d), C.byref(prm), barr, xarr, 0, int(block_threads),
+                               infos)
+    if st not in (PFK_OK, -4, -5):
+        _check(st, ctx.h)
+    out = [infos[j].as_dict() for j in range(nsys)]
+    hs = None
+    if hist is not None:
+        hs = [hist[j][:min(out[j]["history_len"], history)] for j in range(nsys)]
+    return xs, out, hs
 
 
 def storage_vectors(method: str, mmax: int) -> int:

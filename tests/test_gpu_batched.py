@@ -1,0 +1,82 @@
+"""Batched PIPEFCG in one persistent launch (pfk_solve_batched): each system
+against the oracle (envelope protocol), bitwise independence of the batch
+composition, and the FP32 inner-CG preconditioner."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov as K
+from oracle import operators as O
+from oracle import preconditioners as PC
+from tests._parity import check_solve, oracle_with_envelope
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    from paper_1511_07226_gb300 import pfk
+    return pfk.Context(0)
+
+
+def _systems(sides):
+    return [W.batched2d_system(j, s, config_id=4) for j, s in enumerate(sides)]
+
+
+@pytest.mark.parametrize("block_threads", [0, 128, 512])
+def test_batched_systems_match_oracle(ctx, block_threads):
+    from paper_1511_07226_gb300 import pfk
+    sides = [33, 48, 20, 64, 40]
+    sys = _systems(sides)
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys]
+    xs, infos, hists = pfk.solve_batched(ctx, ops, [c["b"] for c in sys], pc_kind="inner_pcg", inner_iters=4,
+                                         precision="fp64", history=2000, block_threads=block_threads, mmax=20,
+                                         rtol=1e-8, maxit=1000)
+    for c, info, h in zip(sys, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.InnerPCG(aop, 4), c["b"],
+                                         K.Params(mmax=20, rtol=1e-8, maxit=1000))
+        check_solve(h, info, ref, alts, rtol=1e-8)
+
+
+def test_batch_composition_does_not_change_results(ctx):
+    from paper_1511_07226_gb300 import pfk
+    sides = [40, 25, 57, 32]
+    sys = _systems(sides)
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys]
+    xs, infos, hists = pfk.solve_batched(ctx, ops, [c["b"] for c in sys], history=2000, block_threads=256,
+                                         mmax=20, rtol=1e-8)
+    for j in (0, 2):
+        x1, i1, h1 = pfk.solve_batched(ctx, [ops[j]], [sys[j]["b"]], history=2000, block_threads=256, mmax=20,
+                                       rtol=1e-8)
+        assert np.array_equal(x1[0], xs[j])
+        assert np.array_equal(h1[0], hists[j], equal_nan=True)
+        assert i1[0]["iterations"] == infos[j]["iterations"]
+
+
+def test_batched_3d_and_jacobi(ctx):
+    from paper_1511_07226_gb300 import pfk
+    cs = [W.poisson3d_gaussian(dims=(14, 12, 10), ell=3.0, log_contrast=2.0, config_id=4, item_id=70 + j)
+          for j in range(3)]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    xs, infos, hists = pfk.solve_batched(ctx, ops, [c["b"] for c in cs], pc_kind="jacobi", history=2000,
+                                         mmax=30, rtol=1e-9, maxit=2000)
+    for c, info, h in zip(cs, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.JacobiPC(aop), c["b"],
+                                         K.Params(mmax=30, rtol=1e-9, maxit=2000))
+        check_solve(h, info, ref, alts, rtol=1e-9)
+
+
+def test_batched_fp32_preconditioner(ctx):
+    """Mixed precision (parity unpinned): FP32 inner CG under FP64 recurrences must
+    still meet the FP64 true-residual tolerance."""
+    from paper_1511_07226_gb300 import pfk
+    sys = _systems([48, 96, 32])
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys]
+    xs, infos, _ = pfk.solve_batched(ctx, ops, [c["b"] for c in sys], precision="fp32", mmax=20, rtol=1e-8)
+    for c, info, x in zip(sys, infos, xs):
+        assert info["status"] == 0
+        assert info["rnorm_true"] <= 1e-8 * info["bnorm"]
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        assert np.linalg.norm(c["b"] - aop.apply(x)) <= 1e-8 * np.linalg.norm(c["b"]) * (1 + 1e-6)
