@@ -201,6 +201,10 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--maxit", type=int, default=10000)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--extras", default="pipegcr,batched,fgmres256,serve",
+                    help="comma-separated secondary measurements (pipegcr, batched, fgmres256, serve) or 'none'")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
     if args.ncu_case:
         from paper_1511_07226_gb300 import pfk
@@ -319,6 +323,13 @@ def main():
                  "true_rel_residual": minfo[-1]["rnorm_true"] / minfo[-1]["bnorm"],
                  "speedup_vs_fp64": ms_max / mms}
 
+    extras = {}
+    wanted = [e for e in args.extras.split(",") if e and e != "none"]
+    if rank == 0:
+        for name in wanted:
+            extras[name] = EXTRAS[name](ctx, dev, args)
+            torch.cuda.synchronize(dev)
+
     if rank != 0:
         return
     cpu = None
@@ -345,12 +356,127 @@ def main():
                      "passes": pinfo["pass_launches"]},
         "gpu_launches": launches,
         "mixed_fp32_pc": mixed,
+        **extras,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Secondary measurements (rank 0): the other workloads of the method
+# ---------------------------------------------------------------------------
+
+def extra_pipegcr(ctx, dev, args) -> dict:
+    """PIPEGCR (Alg. 11), restart 30, on the same 128^3 problem and preconditioner."""
+    import torch
+    from paper_1511_07226_gb300 import pfk
+    c = make_problem()
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4, precision="fp64")
+    b = torch.from_numpy(c["b"]).to(dev)
+    x = torch.zeros_like(b)
+    pfk.solve(ctx, op, pc, b, x0=x, method="pipegcr", mmax=30, rtol=1e-8, maxit=20000)
+    x.zero_()
+    _, info, _ = pfk.solve(ctx, op, pc, b, x0=x, method="pipegcr", mmax=30, rtol=1e-8, maxit=20000)
+    return {"workload": "PIPEGCR restart 30, 128^3 contrast 1e6, 4 inner Jacobi-PCG (FP64), rtol 1e-8",
+            "time_to_1e-8_ms": info["time_ms"], "iterations": info["iterations"], "status": info["status_name"],
+            "true_rel_residual": info["rnorm_true"] / info["bnorm"], "restarts": info["restarts"],
+            "kernel_launches": info["kernel_launches"]}
+
+
+def extra_batched(ctx, dev, args) -> dict:
+    """512 independent 2D systems (sides 32..256) in one persistent PIPEFCG launch."""
+    import workloads as W
+    from paper_1511_07226_gb300 import pfk
+    sides = W.batched2d_sides()
+    sys_ = [W.batched2d_system(j, int(s)) for j, s in enumerate(sides)]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys_]
+    bs = [c["b"] for c in sys_]
+    kw = dict(pc_kind="inner_pcg", inner_iters=4, precision="fp32", mmax=20, rtol=1e-8, maxit=20000)
+    pfk.solve_batched(ctx, ops, bs, **kw)            # autotunes the block size
+    t0 = time.perf_counter()
+    xs, infos, _ = pfk.solve_batched(ctx, ops, bs, **kw)
+    wall = time.perf_counter() - t0
+    kern_ms = max(i["time_ms"] for i in infos)
+    unknowns = int(sum(int(s) ** 2 for s in sides))
+    return {"workload": "512 2D systems, sides U[32,256], contrast 1e4, PIPEFCG nu_max=20, 4 inner CG (FP32)",
+            "systems": len(ops), "unknowns": unknowns, "kernel_ms": kern_ms, "solves_per_s": len(ops) / (kern_ms / 1e3),
+            "e2e_ms": wall * 1e3, "e2e_solves_per_s": len(ops) / wall,
+            "converged": int(sum(i["status_name"] == "ok" for i in infos)),
+            "iterations_median": int(np.median([i["iterations"] for i in infos])),
+            "iterations_max": int(max(i["iterations"] for i in infos)),
+            "max_true_rel_residual": float(max(i["rnorm_true"] / i["bnorm"] for i in infos))}
+
+
+def extra_fgmres256(ctx, dev, args) -> dict:
+    """PIPEFGMRES (Alg. 15) restart 30 on 256^3 two-phase advection-diffusion:
+    8 Chebyshev-Jacobi sweeps with BF16-stored coefficients / FP32 vectors against FP64."""
+    import torch
+    import workloads as W
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_two_phase()
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"], vel=c["vel"])
+    b = torch.from_numpy(c["b"]).to(dev)
+    out = {"workload": "PIPEFGMRES restart 30, 256^3 two-phase eta (1, 1e4), Peclet 10 upwind advection, "
+                       "8 Chebyshev-Jacobi sweeps, rtol 1e-8", "n_unknowns": int(b.numel())}
+    for prec in ("bf16", "fp64"):
+        pc = pfk.Preconditioner(ctx, op, "chebyshev", inner_iters=8, precision=prec)
+        x = torch.zeros_like(b)
+        _, info, _ = pfk.solve(ctx, op, pc, b, x0=x, method="pipefgmres", mmax=30, rtol=1e-8, maxit=20000)
+        out[prec] = {"time_to_1e-8_ms": info["time_ms"], "iterations": info["iterations"],
+                     "status": info["status_name"], "true_rel_residual": info["rnorm_true"] / info["bnorm"]}
+        pc.close()
+    out["speedup_bf16_vs_fp64"] = out["fp64"]["time_to_1e-8_ms"] / out["bf16"]["time_to_1e-8_ms"]
+    return out
+
+
+def extra_serve(ctx, dev, args) -> dict:
+    """A bounded prefix of the Poisson-arrival request stream (mean 200 req/s,
+    3D sides U[32,160], contrast 1e2..1e6, method drawn from PIPEFCG / PIPEGCR /
+    PIPEFGMRES) replayed in real time through the continuous-batching server."""
+    import workloads as W
+    from paper_1511_07226_gb300 import pfk
+    meth = {0: "pipefcg", 1: "pipegcr", 2: "pipefgmres"}
+    reqs = W.request_stream(count=args.serve_requests)
+    probs = [W.request_problem(r) for r in reqs]
+    srv = pfk.Server(ctx, workers=args.serve_workers)
+    kw = dict(mmax=30, rtol=1e-8, maxit=20000)
+    # warm-up: one small request per method (graphs, module loading)
+    for m in meth.values():
+        p = W.poisson3d_gaussian(n=24, ell=4.0, log_contrast=1.0, config_id=5, item_id=999_999)
+        srv.poll(srv.submit(p["dims"], p["eta"], p["b"], method=m, **kw))
+    results = [None] * len(reqs)
+
+    def collect(tickets):
+        for j, t in tickets:
+            results[j] = srv.poll(t)
+
+    tickets = []
+    t0 = time.perf_counter()
+    for j, (r, p) in enumerate(zip(reqs, probs)):
+        delay = r["t"] - reqs[0]["t"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append((j, srv.submit(p["dims"], p["eta"], p["b"], method=meth[r["method"]], **kw)))
+    collect(tickets)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([res[2] for res in results])
+    ok = sum(res[1]["status_name"] == "ok" for res in results)
+    unknowns = int(sum(r["side"] ** 3 for r in reqs))
+    return {"workload": f"first {len(reqs)} requests of the seeded stream, replayed at their arrival times",
+            "workers": args.serve_workers, "requests": len(reqs), "converged": int(ok),
+            "offered_rate_per_s": len(reqs) / max(reqs[-1]["t"] - reqs[0]["t"], 1e-9),
+            "solves_per_s": len(reqs) / wall, "unknowns_per_s": unknowns / wall,
+            "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+            "max_latency_ms": float(lat.max()),
+            "max_true_rel_residual": float(max(res[1]["rnorm_true"] / res[1]["bnorm"] for res in results))}
+
+
+EXTRAS = {"pipegcr": extra_pipegcr, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
 
 
 # Iterations of one 128^3 solve for the reference arm's extrapolation (the FP64

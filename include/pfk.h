@@ -316,6 +316,52 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
                              int ptrs_on_device, int block_threads, pfk_solve_info* infos);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of independent solves                        */
+/* ------------------------------------------------------------------------ */
+
+/* A server accepts solve requests at any time, queues them in arrival order
+ * and admits the head of the queue as soon as a worker is free and the device
+ * memory the active solves hold (operator, preconditioner scratch, Krylov
+ * workspace) plus the new request's estimate fits the budget; a request larger
+ * than the budget still runs when nothing else is active.  Each worker owns a
+ * CUDA stream and runs whole solves (graph-replayed iterations, Krylov basis
+ * resident on the device), so the kernels of active solves overlap on the GPU
+ * and requests join while others are running.  A request's arithmetic does not
+ * depend on the other requests: its result is bit for bit the one a solve of
+ * the same request alone gives.  The server is internally synchronised (any
+ * thread may submit and poll). */
+typedef struct pfk_server pfk_server;
+
+typedef struct {
+  int32_t workers;         /* concurrent solves; 0 = 4 */
+  int32_t queue_capacity;  /* queued + active requests; 0 = 4096 */
+  int64_t memory_budget;   /* device bytes for active solves; 0 = 80 % of free memory */
+} pfk_server_params;
+
+typedef struct {
+  pfk_operator_desc op;     /* host arrays only; copied by pfk_submit */
+  pfk_pc_desc pc;           /* kind PFK_PC_NONE for no preconditioner */
+  pfk_solve_params params;  /* history and profile are ignored */
+  const double* b;          /* host, length n, copied */
+  const double* x0;         /* host or NULL (zero), copied */
+} pfk_request;
+
+/* ctx supplies the device; the server creates its own streams and contexts. */
+pfk_status pfk_server_create(pfk_context* ctx, const pfk_server_params* params, pfk_server** srv);
+/* Queues a request; *ticket identifies it.  PFK_ERR_BUSY when the queue is
+ * full, PFK_ERR_INVALID for a bad description (message: pfk_last_error(NULL)). */
+pfk_status pfk_submit(pfk_server* srv, const pfk_request* req, uint64_t* ticket);
+/* Waits up to wait_ms (< 0: without limit) for the request.  PFK_PENDING if it
+ * is not done yet; otherwise the solve's status, with x_out (host, length n;
+ * may be NULL), info (may be NULL) and latency_ms = submission to completion
+ * (may be NULL) filled in, and the ticket released.  PFK_ERR_INVALID for an
+ * unknown or already collected ticket. */
+pfk_status pfk_poll(pfk_server* srv, uint64_t ticket, double* x_out, pfk_solve_info* info, double* latency_ms,
+                    int wait_ms);
+/* Stops admitting, finishes the active solves, drops queued requests. */
+pfk_status pfk_server_destroy(pfk_server* srv);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free preconditioner application                                */
 /* ------------------------------------------------------------------------ */
 

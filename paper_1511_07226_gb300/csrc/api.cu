@@ -80,6 +80,10 @@ pfk_status pfk_create_context(int device, void* cuda_stream, pfk_context** out) 
     pfk_destroy_context(ctx);
     return cuda_fail(nullptr, e, "cudaStreamCreate (capture stream)");
   }
+  if ((e = cudaMallocHost((void**)&ctx->pinned, 2 * sizeof(SolveCtl))) != cudaSuccess) {
+    pfk_destroy_context(ctx);
+    return cuda_fail(nullptr, e, "cudaMallocHost (status words)");
+  }
   cudaMemset(ctx->scratch_counter, 0, 4 * sizeof(unsigned int));
   cudaDeviceSynchronize();
   *out = ctx;
@@ -90,7 +94,9 @@ pfk_status pfk_destroy_context(pfk_context* ctx) {
   if (!ctx) return PFK_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->ws) cudaFreeAsync(ctx->ws, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->scratch_partials) cudaFree(ctx->scratch_partials);
   if (ctx->scratch_counter) cudaFree(ctx->scratch_counter);
   if (ctx->scratch_out) cudaFree(ctx->scratch_out);
@@ -107,6 +113,7 @@ pfk_status pfk_create_operator(pfk_context* ctx, const pfk_operator_desc* desc, 
   if (!op) return PFK_ERR_OOM;
   op->ctx = ctx;
   op->device = ctx->device;
+  op->stream = ctx->stream;
   op->kind = desc->kind;
   op->storage = desc->storage;
   pfk_status s;
@@ -146,13 +153,16 @@ pfk_status pfk_destroy_operator(pfk_operator* op) {
   if (!op) return PFK_OK;
   // the operator may outlive its context (e.g. finalisation order in a
   // garbage-collected binding): use the device recorded at creation only
+  // (and the stream it was created on, which must outlive it); the frees are
+  // stream-ordered, so destroying an operator does not synchronise the device
   cudaSetDevice(op->device);
-  cudaDeviceSynchronize();
+  cudaStreamSynchronize(op->stream);
   void* ptrs[] = {op->d, op->kx, op->ky, op->kz, op->dinv, op->d32, op->kx32, op->ky32, op->kz32, op->dinv32,
                   op->d16, op->kx16, op->ky16, op->kz16, op->dinv16, op->rowptr, op->colidx, op->vals,
                   op->csr_dinv};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, op->stream);
+  cudaStreamSynchronize(op->stream);
   delete op;
   return PFK_OK;
 }
@@ -180,6 +190,7 @@ pfk_status pfk_create_preconditioner(pfk_context* ctx, const pfk_operator* op, c
   pfk_pc* pc = new (std::nothrow) pfk_pc();
   if (!pc) return PFK_ERR_OOM;
   pc->device = ctx->device;
+  pc->stream = ctx->stream;
   pfk_status s = create_pc(ctx, op, desc, pc);
   if (s != PFK_OK) {
     pfk_destroy_preconditioner(pc);
@@ -193,10 +204,11 @@ pfk_status pfk_destroy_preconditioner(pfk_pc* pc) {
   if (!pc) return PFK_OK;
   // as for operators: never dereference the (possibly destroyed) context
   cudaSetDevice(pc->device);
-  cudaDeviceSynchronize();
-  if (pc->buf) cudaFree(pc->buf);
-  if (pc->ctl) cudaFree(pc->ctl);
-  if (pc->partials) cudaFree(pc->partials);
+  cudaStreamSynchronize(pc->stream);
+  if (pc->buf) cudaFreeAsync(pc->buf, pc->stream);
+  if (pc->ctl) cudaFreeAsync(pc->ctl, pc->stream);
+  if (pc->partials) cudaFreeAsync(pc->partials, pc->stream);
+  cudaStreamSynchronize(pc->stream);
   delete pc;
   return PFK_OK;
 }

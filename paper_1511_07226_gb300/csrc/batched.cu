@@ -621,14 +621,6 @@ static int blocks_per_sm(int tmpl, int T, size_t smem) {
 
 using namespace pfk;
 
-namespace {
-// Autotuned block sizes, keyed by (mmax template, log2 of the largest system, count bucket).
-std::map<std::tuple<pfk_context*, int, int, int, int>, int>& tuned() {
-  static std::map<std::tuple<pfk_context*, int, int, int, int>, int> m;
-  return m;
-}
-}  // namespace
-
 extern "C" pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* const* ops,
                                         const pfk_pc_desc* pcd, const pfk_solve_params* prm, const double* const* b,
                                         double* const* x, int ptrs_on_device, int block_threads,
@@ -741,11 +733,11 @@ extern "C" pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_op
   auto valid_T = [&](int T) { return smem_of(T) <= 227 * 1024; };
   int T = block_threads;
   const int lg = (int)std::ceil(std::log2((double)std::max<int64_t>(nmax, 2)));
-  const auto key = std::make_tuple(ctx, tmpl, lg, nsys >= 4 * ctx->num_sms ? 2 : (nsys >= ctx->num_sms ? 1 : 0),
+  const auto key = std::make_tuple(tmpl, lg, nsys >= 4 * ctx->num_sms ? 2 : (nsys >= ctx->num_sms ? 1 : 0),
                                    (int)fp32 + 2 * P.pc_inner);
   if (T == 0) {
-    auto it = tuned().find(key);
-    if (it != tuned().end()) T = it->second;
+    auto it = ctx->batched_tuned.find(key);
+    if (it != ctx->batched_tuned.end()) T = it->second;
   }
   std::vector<double> xsave;
   if (T == 0) {
@@ -789,7 +781,7 @@ extern "C" pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_op
       set_error(ctx, "no block size fits the batched kernel");
       return PFK_ERR_INVALID;
     }
-    tuned()[key] = T;
+    ctx->batched_tuned[key] = T;
   }
   if (!valid_T(T)) {
     set_error(ctx, "block_threads too large for the window's shared memory");

@@ -12,7 +12,9 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pfk.h"
@@ -91,11 +93,16 @@ struct pfk_context {
   double* scratch_partials = nullptr;   // reduction partials for standalone calls
   unsigned int* scratch_counter = nullptr;
   double* scratch_out = nullptr;
+  pfk::SolveCtl* pinned = nullptr;      // host-pinned status copies of pfk_solve
+  // block sizes autotuned by pfk_solve_batched, keyed by (mmax template, log2 of
+  // the largest system, count bucket, preconditioner precision + 2 x inner iterations)
+  std::map<std::tuple<int, int, int, int>, int> batched_tuned;
 };
 
 struct pfk_operator {
   pfk_context* ctx = nullptr;   // used while the context lives; destruction uses `device`
   int device = 0;
+  cudaStream_t stream = nullptr;
   int kind = 0;
   int storage = 0;
   int nx = 0, ny = 0, nz = 0, ndim = 0;
@@ -131,6 +138,7 @@ struct pfk_operator {
 struct pfk_pc {
   pfk_context* ctx = nullptr;   // used while the context lives; destruction uses `device`
   int device = 0;
+  cudaStream_t stream = nullptr;
   const pfk_operator* op = nullptr;
   int kind = 0;
   int inner = 0;

@@ -1,0 +1,291 @@
+// Serving loop: continuous batching of independent solves (host runtime).
+//
+// Requests are copied at submission and queued in arrival order.  Worker
+// threads, each with its own CUDA stream and pfk_context, admit the head of the
+// queue when the device-memory budget allows (memory of the active solves is
+// accounted from each request's estimate), run the whole solve through the
+// graph-replayed single-system path, publish the result and release the
+// memory.  Kernels of the active solves run concurrently on the GPU; a request
+// that arrives while others run is admitted as soon as a worker and memory are
+// free.  Nothing in a solve depends on the others, so results are bitwise
+// those of the same request solved alone.
+#include "pfk_internal.cuh"
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace pfk {
+void set_error(pfk_context* ctx, const std::string& msg);
+}
+
+using namespace pfk;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Item {
+  uint64_t ticket = 0;
+  pfk_operator_desc desc{};
+  std::vector<double> eta, vals, b, x;
+  std::vector<int32_t> rowptr, colidx;
+  pfk_pc_desc pc{};
+  pfk_solve_params prm{};
+  int64_t n = 0;
+  int64_t bytes = 0;
+  Clock::time_point t_submit;
+  double latency_ms = 0.0;
+  pfk_solve_info info{};
+  pfk_status status = PFK_PENDING;
+  bool done = false;
+};
+
+}  // namespace
+
+struct pfk_server {
+  int device = 0;
+  int64_t budget = 0;
+  int64_t in_use = 0;
+  int active = 0;
+  int capacity = 0;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::deque<std::shared_ptr<Item>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<Item>> items;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+// Device bytes a request holds while active: operator coefficients (and the
+// preconditioner's reduced copies), preconditioner scratch, the solve
+// workspace, reduction partials and host-staging buffers.
+int64_t estimate_bytes(const Item& it, int num_sms) {
+  const int64_t n = it.n;
+  int64_t op = 0;
+  if (it.desc.kind == PFK_CSR) op = it.desc.nnz * 12 + (n + 1) * 4 + n * 8;
+  else op = 5 * n * 8;
+  int64_t pc = 0;
+  if (it.pc.kind == PFK_PC_INNER_PCG || it.pc.kind == PFK_PC_CHEBYSHEV) {
+    const int64_t es = it.pc.precision == PFK_FP64 ? 8 : 4;
+    pc = 5 * n * es + (it.pc.precision == PFK_FP32 ? 5 * n * 4 : it.pc.precision == PFK_BF16_COEF_FP32 ? 5 * n * 2 : 0);
+  }
+  int64_t ws = 0;
+  if (pfk_solve_workspace_bytes(it.prm.method, it.prm.mmax, n, &ws) != PFK_OK) ws = 0;
+  const int64_t partials = (int64_t)num_sms * kMaxBlocksPerSm * kPartialStride * 8 + 64 * 1024;
+  return op + pc + ws + partials + 2 * n * 8;
+}
+
+void worker_main(pfk_server* srv, int index) {
+  (void)index;
+  cudaSetDevice(srv->device);
+  cudaStream_t stream = nullptr;
+  pfk_context* ctx = nullptr;
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+      pfk_create_context(srv->device, stream, &ctx) != PFK_OK) {
+    ctx = nullptr;
+  }
+  for (;;) {
+    std::shared_ptr<Item> it;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      srv->cv_work.wait(lk, [&] {
+        if (srv->stop) return true;
+        if (srv->queue.empty()) return false;
+        const auto& head = srv->queue.front();
+        return srv->active == 0 || srv->in_use + head->bytes <= srv->budget;
+      });
+      if (srv->stop) break;
+      it = srv->queue.front();
+      srv->queue.pop_front();
+      srv->in_use += it->bytes;
+      srv->active += 1;
+    }
+    pfk_status st = PFK_ERR_CUDA;
+    pfk_solve_info info{};
+    if (ctx) {
+      pfk_operator* op = nullptr;
+      pfk_pc* pc = nullptr;
+      st = pfk_create_operator(ctx, &it->desc, &op);
+      if (st == PFK_OK && it->pc.kind != PFK_PC_NONE) st = pfk_create_preconditioner(ctx, op, &it->pc, &pc);
+      if (st == PFK_OK) st = pfk_solve(ctx, op, pc, &it->prm, it->b.data(), it->x.data(), 0, &info);
+      pfk_destroy_preconditioner(pc);
+      pfk_destroy_operator(op);
+      // the workspace belongs to this request's budget: give it back
+      if (ctx->ws) {
+        cudaFreeAsync(ctx->ws, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+      }
+    }
+    if (st != PFK_OK && info.status == PFK_OK) info.status = st;
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      it->status = st;
+      it->info = info;
+      it->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - it->t_submit).count();
+      it->done = true;
+      it->eta.clear();
+      it->eta.shrink_to_fit();
+      it->b.clear();
+      it->b.shrink_to_fit();
+      srv->in_use -= it->bytes;
+      srv->active -= 1;
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+  }
+  if (ctx) pfk_destroy_context(ctx);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+pfk_status pfk_server_create(pfk_context* ctx, const pfk_server_params* params, pfk_server** out) {
+  if (!ctx || !out) {
+    set_error(ctx, "NULL argument");
+    return PFK_ERR_INVALID;
+  }
+  *out = nullptr;
+  pfk_server* srv = new (std::nothrow) pfk_server();
+  if (!srv) return PFK_ERR_OOM;
+  srv->device = ctx->device;
+  const int workers = params && params->workers > 0 ? params->workers : 4;
+  srv->capacity = params && params->queue_capacity > 0 ? params->queue_capacity : 4096;
+  int64_t budget = params ? params->memory_budget : 0;
+  if (budget <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaSetDevice(ctx->device);
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      delete srv;
+      set_error(ctx, "cudaMemGetInfo failed");
+      return PFK_ERR_CUDA;
+    }
+    budget = (int64_t)(0.8 * (double)fr);
+  }
+  srv->budget = budget;
+  for (int w = 0; w < workers; ++w) srv->workers.emplace_back(worker_main, srv, w);
+  *out = srv;
+  return PFK_OK;
+}
+
+pfk_status pfk_submit(pfk_server* srv, const pfk_request* req, uint64_t* ticket) {
+  if (!srv || !req || !ticket || !req->b) {
+    set_error(nullptr, "NULL argument");
+    return PFK_ERR_INVALID;
+  }
+  auto it = std::make_shared<Item>();
+  it->desc = req->op;
+  it->pc = req->pc;
+  it->prm = req->params;
+  it->prm.history = nullptr;
+  it->prm.history_capacity = 0;
+  it->prm.profile = 0;
+  int64_t n = 0;
+  if (req->op.kind == PFK_STENCIL5_2D || req->op.kind == PFK_STENCIL7_3D) {
+    if (!req->op.eta || req->op.eta_on_device || req->op.nx <= 0 || req->op.ny <= 0) {
+      set_error(nullptr, "requests need host stencil coefficients");
+      return PFK_ERR_INVALID;
+    }
+    n = (int64_t)req->op.nx * req->op.ny * (req->op.kind == PFK_STENCIL5_2D ? 1 : req->op.nz);
+    if (n <= 0) {
+      set_error(nullptr, "invalid stencil size");
+      return PFK_ERR_INVALID;
+    }
+    it->eta.assign(req->op.eta, req->op.eta + n);
+    it->desc.eta = it->eta.data();
+  } else if (req->op.kind == PFK_CSR) {
+    if (req->op.csr_on_device || !req->op.rowptr || req->op.n <= 0) {
+      set_error(nullptr, "requests need host CSR arrays");
+      return PFK_ERR_INVALID;
+    }
+    n = req->op.n;
+    it->rowptr.assign(req->op.rowptr, req->op.rowptr + n + 1);
+    it->colidx.assign(req->op.colidx, req->op.colidx + req->op.nnz);
+    it->vals.assign(req->op.vals, req->op.vals + req->op.nnz);
+    it->desc.rowptr = it->rowptr.data();
+    it->desc.colidx = it->colidx.data();
+    it->desc.vals = it->vals.data();
+  } else {
+    set_error(nullptr, "unknown operator kind");
+    return PFK_ERR_INVALID;
+  }
+  if (it->prm.mmax < 1 || it->prm.mmax > PFK_MAX_MMAX) {
+    set_error(nullptr, "mmax out of range");
+    return PFK_ERR_INVALID;
+  }
+  it->n = n;
+  it->b.assign(req->b, req->b + n);
+  if (req->x0) it->x.assign(req->x0, req->x0 + n);
+  else it->x.assign(n, 0.0);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, srv->device);
+  it->bytes = estimate_bytes(*it, sms);
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if ((int)srv->items.size() >= srv->capacity) {
+      set_error(nullptr, "server queue is full");
+      return PFK_ERR_BUSY;
+    }
+    it->ticket = srv->next_ticket++;
+    it->t_submit = Clock::now();
+    srv->items[it->ticket] = it;
+    srv->queue.push_back(it);
+    *ticket = it->ticket;
+  }
+  srv->cv_work.notify_one();
+  return PFK_OK;
+}
+
+pfk_status pfk_poll(pfk_server* srv, uint64_t ticket, double* x_out, pfk_solve_info* info, double* latency_ms,
+                    int wait_ms) {
+  if (!srv) {
+    set_error(nullptr, "NULL argument");
+    return PFK_ERR_INVALID;
+  }
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto f = srv->items.find(ticket);
+  if (f == srv->items.end()) {
+    set_error(nullptr, "unknown or already collected ticket");
+    return PFK_ERR_INVALID;
+  }
+  std::shared_ptr<Item> it = f->second;
+  if (!it->done) {
+    if (wait_ms == 0) return PFK_PENDING;
+    if (wait_ms < 0) srv->cv_done.wait(lk, [&] { return it->done; });
+    else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return it->done; }))
+      return PFK_PENDING;
+  }
+  if (x_out) std::memcpy(x_out, it->x.data(), sizeof(double) * it->n);
+  if (info) *info = it->info;
+  if (latency_ms) *latency_ms = it->latency_ms;
+  srv->items.erase(ticket);
+  return it->status;
+}
+
+pfk_status pfk_server_destroy(pfk_server* srv) {
+  if (!srv) return PFK_OK;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+    srv->queue.clear();
+  }
+  srv->cv_work.notify_all();
+  for (auto& t : srv->workers) t.join();
+  delete srv;
+  return PFK_OK;
+}
+
+}  // extern "C"

@@ -227,12 +227,7 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
     if (e != cudaSuccess) return cuda_fail(ctx, e, "capture iteration");
   }
 
-  SolveCtl* hc = nullptr;   // pinned status copies
-  PFK_CUDA(ctx, cudaMallocHost((void**)&hc, 2 * sizeof(SolveCtl)));
-  struct HostGuard {
-    SolveCtl* p;
-    ~HostGuard() { if (p) cudaFreeHost(p); }
-  } hguard{hc};
+  SolveCtl* hc = ctx->pinned;   // pinned status copies (owned by the context)
   Events ev, tev;
   PFK_CUDA(ctx, ev.make(2, cudaEventDisableTiming));
   PFK_CUDA(ctx, tev.make(2, cudaEventDefault));

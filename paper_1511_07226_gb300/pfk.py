@@ -51,6 +51,15 @@ class SolveParams(C.Structure):
                 ("history", C.c_void_p), ("history_capacity", C.c_int32), ("profile", C.c_int32)]
 
 
+class ServerParams(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("queue_capacity", C.c_int32), ("memory_budget", C.c_int64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("op", OperatorDesc), ("pc", PcDesc), ("params", SolveParams), ("b", C.c_void_p),
+                ("x0", C.c_void_p)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("restarts", C.c_int32),
                 ("breakdowns", C.c_int32), ("replacements", C.c_int32), ("history_len", C.c_int32),
@@ -89,6 +98,11 @@ _SIGS = {
     "pfk_solve_batched": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(PcDesc),
                                     C.POINTER(SolveParams), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                                     C.c_int, C.POINTER(SolveInfo)]),
+    "pfk_server_create": (C.c_int, [C.c_void_p, C.POINTER(ServerParams), C.POINTER(C.c_void_p)]),
+    "pfk_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "pfk_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(SolveInfo), C.POINTER(C.c_double),
+                           C.c_int]),
+    "pfk_server_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -383,6 +397,72 @@ def solve_batched(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_it
     if hist is not None:
         hs = [hist[j][:min(out[j]["history_len"], history)] for j in range(nsys)]
     return xs, out, hs
+
+
+class Server:
+    """Continuous-batching solve server (pfk_server_*): submit requests at any
+    time, poll for results.  Requests carry host arrays, which are copied at
+    submission; each result is bitwise that of the same request solved alone."""
+
+    def __init__(self, ctx: Context, workers: int = 4, queue_capacity: int = 0, memory_budget: int = 0):
+        self.ctx = ctx
+        p = ServerParams()
+        p.workers, p.queue_capacity, p.memory_budget = int(workers), int(queue_capacity), int(memory_budget)
+        h = C.c_void_p()
+        _check(load().pfk_server_create(ctx.h, C.byref(p), C.byref(h)), ctx.h)
+        self.h = h
+        self._n = {}
+
+    def submit(self, dims, eta, b, x0=None, vel=(0.0, 0.0, 0.0), pc_kind="inner_pcg", inner_iters=4,
+               precision="fp64", **kw) -> int:
+        """Queues the stencil problem -div(eta grad u) (+ advection vel) = b; returns the ticket."""
+        nx, ny, nz = (tuple(int(d) for d in dims) + (1, 1))[:3]
+        r = Request()
+        r.op.kind = OP_KINDS["stencil3d" if nz > 1 else "stencil2d"]
+        r.op.nx, r.op.ny, r.op.nz = nx, ny, nz
+        e = np.ascontiguousarray(eta, dtype=np.float64)
+        r.op.eta, r.op.eta_on_device = e.ctypes.data, 0
+        for i in range(3):
+            r.op.vel[i] = float((tuple(vel) + (0.0, 0.0, 0.0))[i])
+        r.pc.kind = PC_KINDS[pc_kind]
+        r.pc.inner_iters = int(inner_iters)
+        r.pc.precision = PRECISIONS[precision]
+        r.params = make_params(**kw)
+        bh = np.ascontiguousarray(b, dtype=np.float64)
+        r.b = bh.ctypes.data
+        xh = None
+        if x0 is not None:
+            xh = np.ascontiguousarray(x0, dtype=np.float64)
+            r.x0 = xh.ctypes.data
+        t = C.c_uint64()
+        _check(load().pfk_submit(self.h, C.byref(r), C.byref(t)))
+        self._n[int(t.value)] = bh.size
+        return int(t.value)
+
+    def poll(self, ticket: int, wait_ms: int = -1):
+        """(x, info dict, latency_ms) once the request is done, None while pending."""
+        x = np.empty(self._n[ticket])
+        info = SolveInfo()
+        lat = C.c_double()
+        st = load().pfk_poll(self.h, C.c_uint64(ticket), C.c_void_p(x.ctypes.data), C.byref(info), C.byref(lat),
+                             int(wait_ms))
+        if st == PFK_PENDING:
+            return None
+        if st not in (PFK_OK, -4, -5):
+            _check(st)
+        del self._n[ticket]
+        return x, info.as_dict(), float(lat.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pfk_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def storage_vectors(method: str, mmax: int) -> int:

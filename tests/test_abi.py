@@ -68,3 +68,32 @@ def test_struct_layouts():
     assert C.sizeof(pfk.PcDesc) == 32
     assert C.sizeof(pfk.SolveParams) == 72
     assert C.sizeof(pfk.SolveInfo) == 96
+
+
+def _ctypes_layouts():
+    structs = {"pfk_operator_desc": pfk.OperatorDesc, "pfk_pc_desc": pfk.PcDesc,
+               "pfk_solve_params": pfk.SolveParams, "pfk_solve_info": pfk.SolveInfo,
+               "pfk_server_params": pfk.ServerParams, "pfk_request": pfk.Request}
+    return structs
+
+
+def test_struct_layouts_match_c_header(tmp_path):
+    """Every ctypes structure has the size and field offsets the C compiler gives
+    the header's structure."""
+    structs = _ctypes_layouts()
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{pfk.HEADER}"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line)
+    for cname, cls in structs.items():
+        assert int(got[cname]) == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)

@@ -1,0 +1,107 @@
+"""The continuous-batching server (pfk_server_*): every served result is bit for
+bit the result of the same request solved alone through pfk_solve, whatever
+else runs concurrently; admission, queue limit and ticket handling."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import operators as O
+
+pytestmark = pytest.mark.gpu
+
+METHOD_OF = {0: "pipefcg", 1: "pipegcr", 2: "pipefgmres"}
+KW = dict(mmax=30, rtol=1e-8, maxit=3000)
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    from paper_1511_07226_gb300 import pfk
+    return pfk.Context(0)
+
+
+def _requests(count, lo=12, hi=36):
+    out = []
+    for r in W.request_stream(count=count, side_lo=lo, side_hi=hi):
+        c = W.request_problem(r, ell=4.0)
+        out.append((r, c))
+    return out
+
+
+def _alone(ctx, c, method):
+    from paper_1511_07226_gb300 import pfk
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
+    x, info, _ = pfk.solve(ctx, op, pc, c["b"], method=method, **KW)
+    return x, info
+
+
+@pytest.mark.parametrize("workers", [1, 4])
+def test_served_results_equal_solves_alone(ctx, workers):
+    from paper_1511_07226_gb300 import pfk
+    reqs = _requests(10)
+    srv = pfk.Server(ctx, workers=workers)
+    tickets = [srv.submit(c["dims"], c["eta"], c["b"], method=METHOD_OF[r["method"]], **KW) for r, c in reqs]
+    got = [srv.poll(t) for t in tickets]
+    srv.close()
+    for (r, c), (x, info, lat) in zip(reqs, got):
+        method = METHOD_OF[r["method"]]
+        xa, ia = _alone(ctx, c, method)
+        assert info["status_name"] == ia["status_name"] == "ok", (method, info, ia)
+        assert info["iterations"] == ia["iterations"]
+        assert np.array_equal(x, xa), method
+        assert lat > 0.0
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        res = np.linalg.norm(c["b"] - aop.apply(x)) / np.linalg.norm(c["b"])
+        assert res < 1e-6, (method, res)
+
+
+def test_tiny_budget_admits_one_at_a_time_in_order(ctx):
+    """With a budget below any request's estimate, a request is admitted only
+    when nothing else is active: requests finish in arrival order."""
+    from paper_1511_07226_gb300 import pfk
+    reqs = _requests(6, 16, 28)
+    srv = pfk.Server(ctx, workers=4, memory_budget=1)
+    t0 = []
+    tickets = []
+    for r, c in reqs:
+        t0.append(time.perf_counter())
+        tickets.append(srv.submit(c["dims"], c["eta"], c["b"], method=METHOD_OF[r["method"]], **KW))
+    done = []
+    for t, ts in zip(tickets, t0):
+        x, info, lat = srv.poll(t)
+        assert info["status_name"] == "ok"
+        done.append(ts + lat / 1e3)
+    srv.close()
+    # completion instants (submission + latency) do not decrease, up to clock jitter
+    assert all(b >= a - 2e-3 for a, b in zip(done, done[1:])), np.diff(done)
+
+
+def test_queue_capacity_and_tickets(ctx):
+    from paper_1511_07226_gb300 import pfk
+    (r, c), = _requests(1, 12, 12)
+    srv = pfk.Server(ctx, workers=1, queue_capacity=2)
+    a = srv.submit(c["dims"], c["eta"], c["b"], **KW)
+    b = srv.submit(c["dims"], c["eta"], c["b"], **KW)
+    with pytest.raises(pfk.PfkError, match="busy"):
+        srv.submit(c["dims"], c["eta"], c["b"], **KW)
+    xa, _, _ = srv.poll(a)
+    xb, _, _ = srv.poll(b)
+    assert np.array_equal(xa, xb)
+    with pytest.raises(KeyError):
+        srv.poll(a)
+    # a slot frees once a result is collected
+    t = srv.submit(c["dims"], c["eta"], c["b"], **KW)
+    assert srv.poll(t) is not None
+    srv.close()
+
+
+def test_pending_poll_and_destroy_with_queued_requests(ctx):
+    from paper_1511_07226_gb300 import pfk
+    reqs = _requests(4, 40, 48)
+    srv = pfk.Server(ctx, workers=1)
+    tickets = [srv.submit(c["dims"], c["eta"], c["b"], method="pipefcg", **KW) for r, c in reqs]
+    # the last of four sequential solves cannot be done right after submission
+    assert srv.poll(tickets[-1], wait_ms=0) is None
+    srv.close()   # finishes the active solve, drops the queued ones
