@@ -50,7 +50,8 @@ typedef enum {
   PFK_ERR_OOM = -2,           /* device allocation failed */
   PFK_ERR_CUDA = -3,          /* a CUDA call failed; the message has the CUDA error */
   PFK_ERR_BREAKDOWN = -4,     /* norm breakdown that restarting could not cure (Sec. 5) */
-  PFK_ERR_NOT_CONVERGED = -5, /* maxit reached; x holds the last iterate */
+  PFK_ERR_NOT_CONVERGED = -5, /* maxit reached, or the true residual stayed above the goal after
+                                 max_restarts residual replacements; x holds the last iterate */
   PFK_ERR_TIMEOUT = -6,       /* a bounded device or host wait gave up */
   PFK_ERR_CANCELLED = -7,
   PFK_ERR_BUSY = -8           /* server queue full */

@@ -29,7 +29,9 @@ design notes with its reason):
   the first fill; for the GMRES family the least-squares residual estimate.
   At convergence the true residual ||b - A x||_2 must be <= rtol ||b||_2,
   otherwise the solver restarts from x with its target tightened by
-  0.5 rtol ||b|| / ||b - A x|| (residual replacement).
+  0.5 rtol ||b|| / ||b - A x|| (residual replacement).  When the true
+  residual still misses the goal after ``max_restarts`` restarts the solve
+  ends with status "stagnated" (x is the last iterate).
 * Norm breakdown (eta_i <= 0, or t < 0 for the GMRES family) restarts the
   method from the current x, flushing the pipeline (Sec. 5).  A breakdown in a
   fill, or in the first iteration after a breakdown restart, or more than
@@ -61,7 +63,7 @@ class Params:
 @dataclass
 class Result:
     x: np.ndarray
-    status: str = "running"      # converged | maxit | breakdown
+    status: str = "running"      # converged | maxit | breakdown | stagnated
     iterations: int = 0
     restarts: int = 0
     breakdowns: int = 0
@@ -71,6 +73,7 @@ class Result:
     rho0: float = float("nan")
     rnorm_true: float = float("nan")
     bnorm: float = float("nan")
+    stagnated: bool = False
     history: list = field(default_factory=list)
     trace: list = field(default_factory=list)
 
@@ -119,7 +122,10 @@ class _Monitor:
         if not self.prm.true_residual_check:
             return True
         goal = max(self.prm.rtol * self.res.bnorm, self.prm.atol)
-        if rt <= goal or self.res.restarts >= self.prm.max_restarts:
+        if rt <= goal:
+            return True
+        if self.res.restarts >= self.prm.max_restarts:
+            self.res.stagnated = True
             return True
         self.res.replacements += 1
         self.res.restarts += 1
@@ -128,6 +134,8 @@ class _Monitor:
 
     def finish(self, x, status):
         self.res.x = x
+        if status == "converged" and self.res.stagnated:
+            status = "stagnated"
         self.res.status = status
         if np.isnan(self.res.rnorm_true) or status != "converged":
             self.res.rnorm_true = float(np.linalg.norm(self.b - self.A(x)))

@@ -493,8 +493,10 @@ __device__ void sys_solve(const BatchSys& S, const BatchParams& P, double* smem,
       if (threadIdx.x == 0) {
         const double rt = sqrt(st->red[0]);
         st->rtrue = rt;
-        if (!P.true_check || rt <= st->goal || st->restarts >= P.max_restarts) {
+        if (!P.true_check || rt <= st->goal) {
           st->status = -100;    // accepted
+        } else if (st->restarts >= P.max_restarts) {
+          st->status = -102;    // true residual stagnates above the goal
         } else {
           st->replacements += 1;
           st->restarts += 1;
@@ -505,6 +507,7 @@ __device__ void sys_solve(const BatchSys& S, const BatchParams& P, double* smem,
       }
       __syncthreads();
       if (st->status == -100) { result = PFK_OK; break; }
+      if (st->status == -102) { result = PFK_ERR_NOT_CONVERGED; break; }
       continue;
     }
     if (status == kBreakdown) {

@@ -326,8 +326,13 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
       double rt = 0.0;
       PFK_CUDA(ctx, true_residual(&rt));
       rnorm_true = rt;
-      if (!prm->true_residual_check || rt <= goal || restarts >= prm->max_restarts) {
+      if (!prm->true_residual_check || rt <= goal) {
         result = PFK_OK;
+        break;
+      }
+      if (restarts >= prm->max_restarts) {
+        set_error(ctx, "true residual above the goal after max_restarts residual replacements");
+        result = PFK_ERR_NOT_CONVERGED;
         break;
       }
       replacements += 1;

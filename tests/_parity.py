@@ -78,7 +78,7 @@ def envelope(ref, alts) -> np.ndarray:
     return np.maximum.accumulate(env)
 
 
-def check_solve(hist, info, ref, alts, rtol=None, min_prefix=3):
+def check_solve(hist, info, ref, alts, rtol=None, min_prefix=3, check_status=True):
     """Applies the protocol; returns a summary dict (asserts on failure)."""
     r = ref.rho()
     env = envelope(ref, alts)
@@ -96,8 +96,8 @@ def check_solve(hist, info, ref, alts, rtol=None, min_prefix=3):
     # on the outcome (a stagnating method, e.g. Alg. 7 with a nonlinear
     # preconditioner, can end either way depending on rounding alone)
     spread = max(abs(a.iterations - ref.iterations) for a in alts)
-    if all(a.status == ref.status for a in alts):
-        status = {"converged": 0, "maxit": -5, "breakdown": -4}[ref.status]
+    if check_status and all(a.status == ref.status for a in alts):
+        status = {"converged": 0, "maxit": -5, "stagnated": -5, "breakdown": -4}[ref.status]
         assert info["status"] == status, (info["status"], ref.status)
         band = 2 * spread + 0.05 * ref.iterations + 2
         assert abs(info["iterations"] - ref.iterations) <= band, (info["iterations"], ref.iterations, band)

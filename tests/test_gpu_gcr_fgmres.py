@@ -107,4 +107,30 @@ def test_pipefgmres_breakdown_restarts(ctx):
     x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], method="pipefgmres",
                               mmax=30, sigma=-50.0, rtol=1e-8, maxit=300, max_restarts=5, history=1000)
     assert ref.breakdowns >= 1 and info["breakdowns"] >= 1
-    check_solve(hist, info, ref, alts, min_prefix=1)
+    # after a breakdown restart under this shift, whether the remaining
+    # restarts end in convergence or in another breakdown depends on rounding
+    # alone: the trajectory is checked against the envelope, the outcome for
+    # validity
+    check_solve(hist, info, ref, alts, min_prefix=1, check_status=False)
+    assert info["status_name"] in ("ok", "breakdown")
+    if info["status_name"] == "ok":
+        assert info["rnorm_true"] <= 1e-8 * info["bnorm"] * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("method", ["fcg", "pipefcg", "gcr", "pipegcr"])
+def test_true_residual_stagnation_reported(ctx, method):
+    """A goal below attainable accuracy ends, as in the oracle, with
+    not-converged after max_restarts residual replacements, not with ok."""
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson2d_inclusions(16, 16)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    ref = K.solve(method, aop, PC.JacobiPC(aop), c["b"], prm=K.Params(mmax=10, rtol=1e-18, max_restarts=2,
+                                                                      maxit=2000))
+    assert ref.status == "stagnated"
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "jacobi")
+    x, info, _ = pfk.solve(ctx, op, pc, c["b"], method=method, mmax=10, rtol=1e-18, max_restarts=2, maxit=2000)
+    assert info["status_name"] == "not_converged"
+    assert info["restarts"] == 2
+    assert info["rnorm_true"] / info["bnorm"] < 1e-13
+    assert "true residual" in info["message"]

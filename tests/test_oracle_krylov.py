@@ -329,3 +329,20 @@ def test_sigma_estimate_approaches_largest_eigenvalue():
     est = K.estimate_sigma(op, PC.JacobiPC(op), b, iters=200)
     assert abs(est - lam) <= 1e-3 * lam
     assert K.estimate_sigma(op, PC.JacobiPC(op), b) <= lam * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("method", ["fcg", "pipefcg", "gcr", "pipegcr"])
+def test_true_residual_stagnation_is_not_convergence(method):
+    """A goal below the attainable accuracy: the recurred residual keeps falling
+    but ||b - A x|| stalls at rounding level, so after max_restarts residual
+    replacements the solve reports "stagnated" (x is the last iterate)."""
+    c = W.poisson2d_inclusions(16, 16)
+    A = O.StencilOperator(c["dims"], c["eta"])
+    r = K.solve(method, A, PC.JacobiPC(A), c["b"], prm=K.Params(mmax=10, rtol=1e-18, max_restarts=2, maxit=2000))
+    assert r.status == "stagnated"
+    assert r.restarts == 2 and r.replacements >= 1
+    rel = r.rnorm_true / r.bnorm
+    assert 1e-18 < rel < 1e-13
+    # with an attainable goal the same solve converges
+    r2 = K.solve(method, A, PC.JacobiPC(A), c["b"], prm=K.Params(mmax=10, rtol=1e-10, max_restarts=2))
+    assert r2.status == "converged" and r2.rnorm_true <= 1e-10 * r2.bnorm
