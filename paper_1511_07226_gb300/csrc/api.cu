@@ -84,8 +84,13 @@ pfk_status pfk_create_context(int device, void* cuda_stream, pfk_context** out) 
     pfk_destroy_context(ctx);
     return cuda_fail(nullptr, e, "cudaMallocHost (status words)");
   }
-  cudaMemset(ctx->scratch_counter, 0, 4 * sizeof(unsigned int));
-  cudaDeviceSynchronize();
+  // stream-ordered: no device-wide synchronisation, so a context can be created
+  // while another thread records a CUDA graph
+  if ((e = cudaMemsetAsync(ctx->scratch_counter, 0, 4 * sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    pfk_destroy_context(ctx);
+    return cuda_fail(nullptr, e, "cudaMemsetAsync (context scratch)");
+  }
   *out = ctx;
   return PFK_OK;
 }

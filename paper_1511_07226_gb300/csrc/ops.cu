@@ -6,6 +6,7 @@
 // performance model (Sec. 8): the T_spmv term of every method.  It is the
 // "A" of every listing (Algs. 2-15).
 #include "pfk_internal.cuh"
+#include "stencil.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -121,14 +122,7 @@ __global__ void round_copy_kernel<__nv_bfloat16>(const double* __restrict__ src,
 // Matrix-free stencil application
 // ---------------------------------------------------------------------------
 
-template <typename C>
-__device__ __forceinline__ float coef(C v);
-template <>
-__device__ __forceinline__ float coef<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float coef<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// y = A m (or y = b - A m) in FP64:
+// Stencil geometry and FP64 coefficients (CSR assembly):
 //   (A m)_c = d_c m_c - sum_faces K_f m_nbr - a_d m_up
 struct StencilArgs {
   const double* d;
@@ -141,40 +135,28 @@ struct StencilArgs {
   int64_t n;
 };
 
-__device__ __forceinline__ double stencil_row(const StencilArgs& A, const double* __restrict__ m, int64_t c, int i,
-                                              int j, int k) {
-  const int64_t sxy = (int64_t)A.nx * A.ny;
-  double acc = A.d[c] * m[c];
-  if (i > 0) acc = fma(-(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)), m[c - 1], acc);
-  if (i < A.nx - 1) acc = fma(-(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)), m[c + 1], acc);
-  if (j > 0) acc = fma(-(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)), m[c - A.nx], acc);
-  if (j < A.ny - 1) acc = fma(-(A.ky[c] + (A.u1 == 1 ? A.a1 : 0.0)), m[c + A.nx], acc);
-  if (A.ndim == 3) {
-    if (k > 0) acc = fma(-(A.kz[c - sxy] + (A.u2 == -1 ? A.a2 : 0.0)), m[c - sxy], acc);
-    if (k < A.nz - 1) acc = fma(-(A.kz[c] + (A.u2 == 1 ? A.a2 : 0.0)), m[c + sxy], acc);
+// y = A m (or bsub - A m) with the tiled z-marching walk.
+struct ApplyEpi {
+  double* __restrict__ y;
+  const double* __restrict__ bsub;
+  struct Pre {
+    double b;
+  };
+  __device__ __forceinline__ Pre pre(int64_t c) const { return Pre{bsub ? bsub[c] : 0.0}; }
+  __device__ __forceinline__ void operator()(int64_t c, double v, double, const Pre& p) const {
+    y[c] = bsub ? p.b - v : v;
   }
-  return acc;
-}
+};
 
-// Stencil kernels walk the grid one x-row per warp (lanes along x, coalesced);
-// the row index gives (j, k) with one 32-bit division per row.
-__global__ void __launch_bounds__(kThreads) stencil_apply_kernel(StencilArgs A, const double* __restrict__ m,
-                                                                 double* __restrict__ y,
-                                                                 const double* __restrict__ bsub,
-                                                                 const int* __restrict__ status) {
+template <bool ADV>
+__global__ void __launch_bounds__(kTileThreads) stencil_tiled_apply_kernel(TiledStencil<double, double> A,
+                                                                           const double* __restrict__ m,
+                                                                           double* __restrict__ y,
+                                                                           const double* __restrict__ bsub,
+                                                                           const int* __restrict__ status) {
   if (status && *status != kRun) return;
-  const int lane = threadIdx.x & 31;
-  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-  const int nrows = A.ny * A.nz;
-  for (int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); row < nrows; row += nwarps) {
-    const int j = row % A.ny, k = row / A.ny;
-    const int64_t base = (int64_t)row * A.nx;
-    for (int i = lane; i < A.nx; i += 32) {
-      const int64_t c = base + i;
-      const double v = stencil_row(A, m, c, i, j, k);
-      y[c] = bsub ? bsub[c] - v : v;
-    }
-  }
+  ApplyEpi e{y, bsub};
+  tiled_stencil_walk<double, double, ADV, 1>(A, m, e);
 }
 
 // ---------------------------------------------------------------------------
@@ -274,7 +256,10 @@ cudaError_t op_apply(const pfk_operator* op, const double* x, double* y, const d
   if (op->rowptr) {
     csr_apply_kernel<<<blocks, kThreads, 0, st>>>(op->rowptr, op->colidx, op->vals, x, y, bsub, op->n, status);
   } else {
-    stencil_apply_kernel<<<blocks, kThreads, 0, st>>>(stencil_args(op), x, y, bsub, status);
+    TiledStencil<double, double> A;
+    const int units = tiled_stencil_setup<double, double>(A, op, op->d, op->kx, op->ky, op->kz);
+    if (A.adv) stencil_tiled_apply_kernel<true><<<units, kTileThreads, 0, st>>>(A, x, y, bsub, status);
+    else stencil_tiled_apply_kernel<false><<<units, kTileThreads, 0, st>>>(A, x, y, bsub, status);
   }
   return cudaGetLastError();
 }

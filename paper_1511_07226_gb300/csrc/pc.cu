@@ -19,6 +19,7 @@
 // the FP32 variants accumulate per thread in FP32 and are combined across
 // threads and blocks in FP64.
 #include "pfk_internal.cuh"
+#include "stencil.cuh"
 
 #include <cmath>
 
@@ -48,30 +49,6 @@ struct StencilT {
   int u0, u1, u2;
   int64_t n;
 };
-
-template <typename V, typename C>
-__device__ __forceinline__ V stencil_row_t(const StencilT<V, C>& A, const V* __restrict__ m, int64_t c, int i, int j,
-                                           int k) {
-  const int64_t sxy = (int64_t)A.nx * A.ny;
-  V acc = cv<V, C>(A.d[c]) * m[c];
-  if (i > 0) acc -= (cv<V, C>(A.kx[c - 1]) + (A.u0 == -1 ? A.a0 : V(0))) * m[c - 1];
-  if (i < A.nx - 1) acc -= (cv<V, C>(A.kx[c]) + (A.u0 == 1 ? A.a0 : V(0))) * m[c + 1];
-  if (j > 0) acc -= (cv<V, C>(A.ky[c - A.nx]) + (A.u1 == -1 ? A.a1 : V(0))) * m[c - A.nx];
-  if (j < A.ny - 1) acc -= (cv<V, C>(A.ky[c]) + (A.u1 == 1 ? A.a1 : V(0))) * m[c + A.nx];
-  if (A.ndim == 3) {
-    if (k > 0) acc -= (cv<V, C>(A.kz[c - sxy]) + (A.u2 == -1 ? A.a2 : V(0))) * m[c - sxy];
-    if (k < A.nz - 1) acc -= (cv<V, C>(A.kz[c]) + (A.u2 == 1 ? A.a2 : V(0))) * m[c + sxy];
-  }
-  return acc;
-}
-
-// Stencil loops: one x-row per warp (lanes along x); (j, k) from the row index.
-#define ROW_LOOP(A, c, i, j, k)                                                                   \
-  for (int row_ = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), j = 0, k = 0;               \
-       row_ < (A).ny * (A).nz && ((j = row_ % (A).ny), (k = row_ / (A).ny), true);                 \
-       row_ += (int)((gridDim.x * blockDim.x) >> 5))                                               \
-    for (int i = (int)(threadIdx.x & 31); i < (A).nx; i += 32)                                     \
-      for (int64_t c = (int64_t)row_ * (A).nx + i, once_ = 1; once_; once_ = 0)
 
 #define GRID_LOOP(c, n) \
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (n); c += (int64_t)gridDim.x * blockDim.x)
@@ -153,29 +130,37 @@ __global__ void __launch_bounds__(kThreads) pcg_b_kernel(StencilT<V, C> A, const
 }
 
 // C_i.  s_i = A p_i, eta_i = <s_i, p_i>; finalize alpha_i = gamma_i / eta_i
-// (stop if eta_i == 0).
-template <typename V, typename C>
-__global__ void __launch_bounds__(kThreads) pcg_c_kernel(StencilT<V, C> A, const V* __restrict__ p,
-                                                         V* __restrict__ s, PcCtl* ctl, int i, double* partials,
-                                                         const int* __restrict__ status) {
+// (stop if eta_i == 0).  Tiled z-marching stencil walk.
+template <typename V>
+struct PcgCEpi {
+  V* __restrict__ s;
+  V acc;
+  struct Pre {};
+  __device__ __forceinline__ Pre pre(int64_t) const { return Pre{}; }
+  __device__ __forceinline__ void operator()(int64_t c, V sv, V pv, const Pre&) {
+    s[c] = sv;
+    acc += sv * pv;
+  }
+};
+
+template <typename V, typename C, bool ADV>
+__global__ void __launch_bounds__(kTileThreads) pcg_c_kernel(TiledStencil<V, C> T, const V* __restrict__ p,
+                                                             V* __restrict__ s, PcCtl* ctl, int i, double* partials,
+                                                             const int* __restrict__ status) {
   SKIP_IF_DONE(status);
   if (!(i < ctl->ok)) return;
-  V accv = V(0);
-  ROW_LOOP(A, c, cx, cy, cz) {
-    V sv = stencil_row_t<V, C>(A, p, c, cx, cy, cz);
-    s[c] = sv;
-    accv += sv * p[c];
-  }
-  double acc[1] = {(double)accv};
-  __shared__ double smem[kThreads / 32];
+  PcgCEpi<V> e{s, V(0)};
+  tiled_stencil_walk<V, C, ADV, tiled_width<V, C>()>(T, p, e);
+  double acc[1] = {(double)e.acc};
+  __shared__ double smem[kTileThreads / 32];
   __shared__ double sums[1];
   if (reduce_last_block<1>(acc, 1, partials, 1, &ctl->counter, smem, sums) && threadIdx.x == 0) {
-    const double e = sums[0];
-    if (e == 0.0) {
+    const double eta = sums[0];
+    if (eta == 0.0) {
       ctl->ok = i;
     } else {
-      ctl->eta = e;
-      ctl->alpha[i] = ctl->gamma / e;
+      ctl->eta = eta;
+      ctl->alpha[i] = ctl->gamma / eta;
     }
   }
 }
@@ -207,41 +192,66 @@ __global__ void __launch_bounds__(kThreads) pcg_final_kernel(int64_t n, const V*
 // Chebyshev-Jacobi
 // ---------------------------------------------------------------------------
 
-// Sweep 0 setup: r_0 = v, d_0 = (D^-1 r_0) / theta.
+// Sweep 0 setup: r_0 = v, d_0 = (D^-1 r_0) / theta, as a product with the
+// host-computed 1 / theta (a per-element FP64 division costs a dozen FP64
+// instructions).
 template <typename V, typename C>
 __global__ void __launch_bounds__(kThreads) cheb_init_kernel(StencilT<V, C> A, const double* __restrict__ v,
-                                                             V* __restrict__ r, V* __restrict__ dvec, V theta,
+                                                             V* __restrict__ r, V* __restrict__ dvec, V inv_theta,
                                                              const int* __restrict__ status) {
   SKIP_IF_DONE(status);
   GRID_LOOP(c, A.n) {
     V rv = (V)v[c];
     r[c] = rv;
-    dvec[c] = (cv<V, C>(A.dinv[c]) * rv) / theta;
+    dvec[c] = (cv<V, C>(A.dinv[c]) * rv) * inv_theta;
   }
 }
 
 // Sweep j (j + 1 < k): x_{j+1} = x_j + d_j; r_{j+1} = r_j - A d_j;
-// d_{j+1} = c1 d_j + c2 D^-1 r_{j+1}.  The last sweep only updates x and
-// writes out = add + x_k.
+// d_{j+1} = c1 d_j + c2 D^-1 r_{j+1} (tiled stencil walk over d_j).
 template <typename V, typename C>
-__global__ void __launch_bounds__(kThreads) cheb_sweep_kernel(StencilT<V, C> A, const V* __restrict__ dj,
-                                                              V* __restrict__ dn, V* __restrict__ r,
-                                                              V* __restrict__ x, int j, int last, V c1, V c2,
-                                                              const double* __restrict__ add,
-                                                              double* __restrict__ out,
-                                                              const int* __restrict__ status) {
+struct ChebEpi {
+  const C* __restrict__ dinv;
+  V* __restrict__ dn;
+  V* __restrict__ r;
+  V* __restrict__ x;
+  int first;
+  V c1, c2;
+  struct Pre {
+    V x, r, dinv;
+  };
+  __device__ __forceinline__ Pre pre(int64_t c) const {
+    return Pre{first ? V(0) : x[c], r[c], ld_coef<V, C>(dinv, c)};
+  }
+  __device__ __forceinline__ void operator()(int64_t c, V ad, V dc, const Pre& p) const {
+    x[c] = p.x + dc;
+    const V rv = p.r - ad;
+    r[c] = rv;
+    dn[c] = c1 * dc + c2 * (p.dinv * rv);
+  }
+};
+
+template <typename V, typename C, bool ADV>
+__global__ void __launch_bounds__(kTileThreads, 3) cheb_sweep_kernel(TiledStencil<V, C> T, const C* __restrict__ dinv,
+                                                                  const V* __restrict__ dj, V* __restrict__ dn,
+                                                                  V* __restrict__ r, V* __restrict__ x, int j, V c1,
+                                                                  V c2, const int* __restrict__ status) {
   SKIP_IF_DONE(status);
-  ROW_LOOP(A, c, i, j2, k) {
-    const V dc = dj[c];
-    const V xv = (j == 0 ? V(0) : x[c]) + dc;
-    if (last) {
-      out[c] = add ? add[c] + (double)xv : (double)xv;
-    } else {
-      x[c] = xv;
-      const V rv = r[c] - stencil_row_t<V, C>(A, dj, c, i, j2, k);
-      r[c] = rv;
-      dn[c] = c1 * dc + c2 * (cv<V, C>(A.dinv[c]) * rv);
-    }
+  ChebEpi<V, C> e{dinv, dn, r, x, j == 0, c1, c2};
+  tiled_stencil_walk<V, C, ADV, tiled_width<V, C>()>(T, dj, e);
+}
+
+// Last sweep: out = add + x_{k-1} + d_{k-1} (no operator application).
+template <typename V>
+__global__ void __launch_bounds__(kThreads) cheb_last_kernel(int64_t n, const V* __restrict__ dj,
+                                                             const V* __restrict__ x, int first,
+                                                             const double* __restrict__ add,
+                                                             double* __restrict__ out,
+                                                             const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  GRID_LOOP(c, n) {
+    const V xv = (first ? V(0) : x[c]) + dj[c];
+    out[c] = add ? add[c] + (double)xv : (double)xv;
   }
 }
 
@@ -271,16 +281,23 @@ static cudaError_t inner_pcg(const pfk_pc* pc, StencilT<V, C> A, const double* v
   V* x = base + 2 * n;
   V* p[2] = {base + 3 * n, base + 4 * n};
   const int k = pc->inner;
-  const int blocks = stream_blocks(pc->ctx, n, 2);
+  const int blocks = stream_blocks(pc->ctx, n, 8);
   const int sblocks = stream_blocks(pc->ctx, n, 8);
+  TiledStencil<V, C> T;
+  const int units = tiled_stencil_setup<V, C>(T, pc->op, A.d, A.kx, A.ky, A.kz);
+  const int tblocks = units < pc->partials_cap ? units : pc->partials_cap;
   PcCtl* ctl = pc->ctl;
   pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, 0, k, pc->partials, status);
   pcg_b_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, r, nullptr, p[0], x, ctl, 0, status);
-  pcg_c_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, p[0], s, ctl, 0, pc->partials, status);
+  auto pcg_c = [&](const V* pv, int i) {
+    if (T.adv) pcg_c_kernel<V, C, true><<<tblocks, kTileThreads, 0, st>>>(T, pv, s, ctl, i, pc->partials, status);
+    else pcg_c_kernel<V, C, false><<<tblocks, kTileThreads, 0, st>>>(T, pv, s, ctl, i, pc->partials, status);
+  };
+  pcg_c(p[0], 0);
   for (int i = 1; i < k; ++i) {
     pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, i, k, pc->partials, status);
     pcg_b_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, r, p[(i - 1) & 1], p[i & 1], x, ctl, i, status);
-    pcg_c_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, p[i & 1], s, ctl, i, pc->partials, status);
+    pcg_c(p[i & 1], i);
   }
   pcg_final_kernel<V, C><<<sblocks, kThreads, 0, st>>>(n, p[(k - 1) & 1], x, add, out, ctl, k, status);
   return cudaGetLastError();
@@ -299,15 +316,21 @@ static cudaError_t chebyshev(const pfk_pc* pc, StencilT<V, C> A, const double* v
   const double theta = (pc->hi + pc->lo) / 2.0, delta = (pc->hi - pc->lo) / 2.0;
   const double sigma1 = theta / delta;
   double rho = 1.0 / sigma1;
-  cheb_init_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, v, r, dv[0], (V)theta, status);
-  for (int j = 0; j < k; ++j) {
-    const int last = (j + 1 == k);
+  TiledStencil<V, C> T;
+  const int units = tiled_stencil_setup<V, C>(T, pc->op, A.d, A.kx, A.ky, A.kz);
+  cheb_init_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, v, r, dv[0], (V)(1.0 / theta), status);
+  for (int j = 0; j + 1 < k; ++j) {
     const double rho_new = 1.0 / (2.0 * sigma1 - rho);
     const V c1 = (V)(rho_new * rho), c2 = (V)(2.0 * rho_new / delta);
-    cheb_sweep_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, dv[j & 1], dv[(j + 1) & 1], r, x, j, last, c1, c2, add,
-                                                          out, status);
+    if (T.adv)
+      cheb_sweep_kernel<V, C, true><<<units, kTileThreads, 0, st>>>(T, A.dinv, dv[j & 1], dv[(j + 1) & 1], r, x, j,
+                                                                    c1, c2, status);
+    else
+      cheb_sweep_kernel<V, C, false><<<units, kTileThreads, 0, st>>>(T, A.dinv, dv[j & 1], dv[(j + 1) & 1], r, x, j,
+                                                                     c1, c2, status);
     rho = rho_new;
   }
+  cheb_last_kernel<V><<<sblocks, kThreads, 0, st>>>(n, dv[(k - 1) & 1], x, k == 1, add, out, status);
   return cudaGetLastError();
 }
 
@@ -374,7 +397,9 @@ pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc
     PFK_CUDA(ctx, cudaMallocAsync(&pc->buf, pc->buf_bytes, ctx->stream));
     PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->ctl, sizeof(PcCtl), ctx->stream));
     PFK_CUDA(ctx, cudaMemsetAsync(pc->ctl, 0, sizeof(PcCtl), ctx->stream));
-    PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->partials, (size_t)ctx->num_sms * 8 * sizeof(double), ctx->stream));
+    const int units = tiled_stencil_units(op->nx, op->ny, op->nz, 1);   // the largest unit count (one cell per thread)
+    pc->partials_cap = ctx->num_sms * 8 > units ? ctx->num_sms * 8 : units;
+    PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->partials, (size_t)pc->partials_cap * sizeof(double), ctx->stream));
     if (pc->kind == PFK_PC_CHEBYSHEV) {
       if (desc->cheb_lo == 0.0 && desc->cheb_hi == 0.0) {
         pc->lo = 0.1 * op->gersh;
@@ -482,6 +507,7 @@ extern "C" pfk_status pfk_pc_apply_inner_pcg_noalloc(pfk_context* ctx, const pfk
   tmp.buf = scratch;
   tmp.buf_bytes = 5 * (size_t)op->n * sizeof(double);
   tmp.partials = scratch + 5 * kNoallocMaxN;
+  tmp.partials_cap = (int)kNoallocPartials;
   tmp.ctl = (PcCtl*)(scratch + 5 * kNoallocMaxN + kNoallocPartials);
   // the control block keeps the previous call's values: its arrival counter
   // must start at zero

@@ -149,6 +149,7 @@ struct pfk_pc {
   size_t buf_bytes = 0;
   pfk::PcCtl* ctl = nullptr;
   double* partials = nullptr;
+  int partials_cap = 0;         // doubles in `partials` (bounds the grid of the reduction kernels)
 };
 
 namespace pfk {

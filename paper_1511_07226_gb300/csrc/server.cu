@@ -17,6 +17,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -44,6 +45,7 @@ struct Item {
   double latency_ms = 0.0;
   pfk_solve_info info{};
   pfk_status status = PFK_PENDING;
+  std::string err;
   bool done = false;
 };
 
@@ -62,6 +64,11 @@ struct pfk_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::vector<std::thread> workers;
+  // per worker: stream and context, created before any worker starts and
+  // destroyed after all have stopped, so that no context set-up or teardown
+  // runs while a worker records a CUDA graph
+  std::vector<cudaStream_t> streams;
+  std::vector<pfk_context*> ctxs;
 };
 
 namespace {
@@ -86,14 +93,8 @@ int64_t estimate_bytes(const Item& it, int num_sms) {
 }
 
 void worker_main(pfk_server* srv, int index) {
-  (void)index;
   cudaSetDevice(srv->device);
-  cudaStream_t stream = nullptr;
-  pfk_context* ctx = nullptr;
-  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
-      pfk_create_context(srv->device, stream, &ctx) != PFK_OK) {
-    ctx = nullptr;
-  }
+  pfk_context* ctx = srv->ctxs[index];
   for (;;) {
     std::shared_ptr<Item> it;
     {
@@ -112,6 +113,7 @@ void worker_main(pfk_server* srv, int index) {
     }
     pfk_status st = PFK_ERR_CUDA;
     pfk_solve_info info{};
+    std::string err;
     if (ctx) {
       pfk_operator* op = nullptr;
       pfk_pc* pc = nullptr;
@@ -129,9 +131,11 @@ void worker_main(pfk_server* srv, int index) {
       }
     }
     if (st != PFK_OK && info.status == PFK_OK) info.status = st;
+    if (st != PFK_OK) err = ctx ? pfk_last_error(ctx) : "worker has no context";
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       it->status = st;
+      it->err = err;
       it->info = info;
       it->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - it->t_submit).count();
       it->done = true;
@@ -145,8 +149,15 @@ void worker_main(pfk_server* srv, int index) {
     srv->cv_done.notify_all();
     srv->cv_work.notify_all();
   }
-  if (ctx) pfk_destroy_context(ctx);
-  if (stream) cudaStreamDestroy(stream);
+}
+
+void release_workers(pfk_server* srv) {
+  for (pfk_context* c : srv->ctxs)
+    if (c) pfk_destroy_context(c);
+  for (cudaStream_t s : srv->streams)
+    if (s) cudaStreamDestroy(s);
+  srv->ctxs.clear();
+  srv->streams.clear();
 }
 
 }  // namespace
@@ -176,6 +187,21 @@ pfk_status pfk_server_create(pfk_context* ctx, const pfk_server_params* params, 
     budget = (int64_t)(0.8 * (double)fr);
   }
   srv->budget = budget;
+  cudaSetDevice(ctx->device);
+  for (int w = 0; w < workers; ++w) {
+    cudaStream_t s = nullptr;
+    pfk_context* c = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    pfk_status ps = e == cudaSuccess ? pfk_create_context(ctx->device, s, &c) : PFK_ERR_CUDA;
+    srv->streams.push_back(s);
+    srv->ctxs.push_back(c);
+    if (ps != PFK_OK) {
+      release_workers(srv);
+      delete srv;
+      set_error(ctx, "could not create the worker streams and contexts");
+      return ps;
+    }
+  }
   for (int w = 0; w < workers; ++w) srv->workers.emplace_back(worker_main, srv, w);
   *out = srv;
   return PFK_OK;
@@ -271,6 +297,7 @@ pfk_status pfk_poll(pfk_server* srv, uint64_t ticket, double* x_out, pfk_solve_i
   if (x_out) std::memcpy(x_out, it->x.data(), sizeof(double) * it->n);
   if (info) *info = it->info;
   if (latency_ms) *latency_ms = it->latency_ms;
+  if (it->status != PFK_OK) set_error(nullptr, it->err);
   srv->items.erase(ticket);
   return it->status;
 }
@@ -284,6 +311,7 @@ pfk_status pfk_server_destroy(pfk_server* srv) {
   }
   srv->cv_work.notify_all();
   for (auto& t : srv->workers) t.join();
+  release_workers(srv);
   delete srv;
   return PFK_OK;
 }
