@@ -257,8 +257,11 @@ cudaError_t op_apply(const pfk_operator* op, const double* x, double* y, const d
     csr_apply_kernel<<<blocks, kThreads, 0, st>>>(op->rowptr, op->colidx, op->vals, x, y, bsub, op->n, status);
   } else {
     TiledStencil<double, double> A;
-    const int units = tiled_stencil_setup<double, double>(A, op, op->d, op->kx, op->ky, op->kz);
-    if (A.adv) stencil_tiled_apply_kernel<true><<<units, kTileThreads, 0, st>>>(A, x, y, bsub, status);
+    const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
+    const int slots = adv ? tiled_stencil_slots(stencil_tiled_apply_kernel<true>, op->ctx->num_sms)
+                          : tiled_stencil_slots(stencil_tiled_apply_kernel<false>, op->ctx->num_sms);
+    const int units = tiled_stencil_setup<double, double>(A, op, op->d, op->kx, op->ky, op->kz, slots);
+    if (adv) stencil_tiled_apply_kernel<true><<<units, kTileThreads, 0, st>>>(A, x, y, bsub, status);
     else stencil_tiled_apply_kernel<false><<<units, kTileThreads, 0, st>>>(A, x, y, bsub, status);
   }
   return cudaGetLastError();

@@ -284,7 +284,11 @@ static cudaError_t inner_pcg(const pfk_pc* pc, StencilT<V, C> A, const double* v
   const int blocks = stream_blocks(pc->ctx, n, 8);
   const int sblocks = stream_blocks(pc->ctx, n, 8);
   TiledStencil<V, C> T;
-  const int units = tiled_stencil_setup<V, C>(T, pc->op, A.d, A.kx, A.ky, A.kz);
+  const pfk_operator* op = pc->op;
+  const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
+  const int slots = adv ? tiled_stencil_slots(pcg_c_kernel<V, C, true>, pc->ctx->num_sms)
+                        : tiled_stencil_slots(pcg_c_kernel<V, C, false>, pc->ctx->num_sms);
+  const int units = tiled_stencil_setup<V, C>(T, op, A.d, A.kx, A.ky, A.kz, slots);
   const int tblocks = units < pc->partials_cap ? units : pc->partials_cap;
   PcCtl* ctl = pc->ctl;
   pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, 0, k, pc->partials, status);
@@ -317,7 +321,11 @@ static cudaError_t chebyshev(const pfk_pc* pc, StencilT<V, C> A, const double* v
   const double sigma1 = theta / delta;
   double rho = 1.0 / sigma1;
   TiledStencil<V, C> T;
-  const int units = tiled_stencil_setup<V, C>(T, pc->op, A.d, A.kx, A.ky, A.kz);
+  const pfk_operator* op = pc->op;
+  const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
+  const int slots = adv ? tiled_stencil_slots(cheb_sweep_kernel<V, C, true>, pc->ctx->num_sms)
+                        : tiled_stencil_slots(cheb_sweep_kernel<V, C, false>, pc->ctx->num_sms);
+  const int units = tiled_stencil_setup<V, C>(T, op, A.d, A.kx, A.ky, A.kz, slots);
   cheb_init_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, v, r, dv[0], (V)(1.0 / theta), status);
   for (int j = 0; j + 1 < k; ++j) {
     const double rho_new = 1.0 / (2.0 * sigma1 - rho);
@@ -397,7 +405,7 @@ pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc
     PFK_CUDA(ctx, cudaMallocAsync(&pc->buf, pc->buf_bytes, ctx->stream));
     PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->ctl, sizeof(PcCtl), ctx->stream));
     PFK_CUDA(ctx, cudaMemsetAsync(pc->ctl, 0, sizeof(PcCtl), ctx->stream));
-    const int units = tiled_stencil_units(op->nx, op->ny, op->nz, 1);   // the largest unit count (one cell per thread)
+    const int units = tiled_stencil_max_units(op->nx, op->ny, op->nz);
     pc->partials_cap = ctx->num_sms * 8 > units ? ctx->num_sms * 8 : units;
     PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->partials, (size_t)pc->partials_cap * sizeof(double), ctx->stream));
     if (pc->kind == PFK_PC_CHEBYSHEV) {

@@ -17,6 +17,8 @@
 
 #include "pfk_internal.cuh"
 
+#include <cmath>
+
 namespace pfk {
 
 constexpr int kTileX = 32;
@@ -31,8 +33,9 @@ struct TiledStencil {
   const C* kz;
   int nx, ny, nz;
   int tiles_x, tiles_y, zc, zchunks;   // work decomposition: tiles_x * tiles_y * zchunks units of zc planes
-  V am0, ap0, am1, ap1, am2, ap2;      // upwind additions at the -/+ neighbour of each direction
-  bool adv;                            // any of them non-zero
+  V a0, a1, a2;                        // upwind weights h |v_d| (0: no advection along d)
+  int up0, up1, up2;                   // side of the upwind neighbour: -1 (v_d > 0) or +1
+  bool adv;                            // any weight non-zero
 };
 
 template <typename V, typename C>
@@ -179,13 +182,16 @@ __device__ __forceinline__ void tiled_stencil_walk(const TiledStencil<V, C>& A, 
           acc -= cur.kz[w] * cur.mup[w];
         }
         if (ADV) {
-          if (i > 0) acc -= A.am0 * mxm[w];
-          if (i + 1 < A.nx) acc -= A.ap0 * mxp[w];
-          if (j > 0) acc -= A.am1 * mym;
-          if (j + 1 < A.ny) acc -= A.ap1 * myp;
+          // one upwind neighbour per direction (the other side's weight is
+          // zero): select it, then one FMA; a neighbour outside the domain is
+          // the zero ghost value
+          const V ux = A.up0 < 0 ? (i > 0 ? mxm[w] : V(0)) : (i + 1 < A.nx ? mxp[w] : V(0));
+          const V uy = A.up1 < 0 ? (j > 0 ? mym : V(0)) : (j + 1 < A.ny ? myp : V(0));
+          acc -= A.a0 * ux;
+          acc -= A.a1 * uy;
           if (A.nz > 1) {
-            if (k > 0) acc -= A.am2 * mdn[w];
-            if (k + 1 < A.nz) acc -= A.ap2 * cur.mup[w];
+            const V uz = A.up2 < 0 ? (k > 0 ? mdn[w] : V(0)) : (k + 1 < A.nz ? cur.mup[w] : V(0));
+            acc -= A.a2 * uz;
           }
         }
         epi(c0 + kTileX * w, acc, mc[w], cur.e[w]);
@@ -202,13 +208,47 @@ __device__ __forceinline__ void tiled_stencil_walk(const TiledStencil<V, C>& A, 
   }
 }
 
-// Host: the tile decomposition of an operator.  One block per work unit
-// (a tile and a chunk of zc planes): units are short, so the hardware block
-// scheduler balances them across SMs; the grid size is the unit count.
-inline int tiled_stencil_units(int nx, int ny, int nz, int w, int* zc_out = nullptr) {
-  const int zc = nz >= 64 ? 16 : (nz >= 16 ? 8 : nz);
-  if (zc_out) *zc_out = zc;
-  return ((nx + kTileX * w - 1) / (kTileX * w)) * ((ny + kTileY - 1) / kTileY) * ((nz + zc - 1) / zc);
+// Host: the tile decomposition of an operator.  One block per work unit (a
+// tile and a chunk of zc consecutive planes).  zc is chosen against the
+// number of blocks the GPU holds at once (`slots`): time ~ waves x (zc + 1/2)
+// (half a plane for the priming loads), so the last wave is not mostly empty.
+inline int tiled_stencil_zc(int tiles, int nz, int slots) {
+  if (nz < 4) return nz;
+  int best = nz;
+  double best_cost = 1e300;
+  const int zmax = nz < 32 ? nz : 32;
+  for (int zc = 2; zc <= zmax; ++zc) {
+    const double units = (double)tiles * (double)((nz + zc - 1) / zc);
+    const double cost = std::ceil(units / (double)slots) * (zc + 0.5);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  return best;
+}
+
+inline int tiled_stencil_tiles(int nx, int ny, int w) {
+  return ((nx + kTileX * w - 1) / (kTileX * w)) * ((ny + kTileY - 1) / kTileY);
+}
+
+// Upper bound of the unit count of any decomposition (zc >= 2, one cell per thread).
+inline int tiled_stencil_max_units(int nx, int ny, int nz) {
+  return tiled_stencil_tiles(nx, ny, 1) * (nz < 4 ? 1 : (nz + 1) / 2);
+}
+
+// Blocks of `kernel` (kTileThreads threads) resident on the whole GPU.
+template <typename K>
+int tiled_stencil_slots(K kernel, int num_sms) {
+  static const int per_sm = [&]() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kTileThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      b = 1;
+    }
+    return b < 1 ? 1 : b;
+  }();
+  return per_sm * num_sms;
 }
 
 // Cells per thread along x: FP64 walks are bound by the FP64 pipe (one cell
@@ -221,23 +261,22 @@ __host__ __device__ constexpr int tiled_width() { return (sizeof(V) == 8 || size
 
 template <typename V, typename C>
 int tiled_stencil_setup(TiledStencil<V, C>& A, const pfk_operator* op, const C* d, const C* kx, const C* ky,
-                        const C* kz) {
+                        const C* kz, int slots) {
   A.d = d; A.kx = kx; A.ky = ky; A.kz = kz;
   A.nx = op->nx; A.ny = op->ny; A.nz = op->nz;
   constexpr int W = tiled_width<V, C>();
   A.tiles_x = (op->nx + kTileX * W - 1) / (kTileX * W);
   A.tiles_y = (op->ny + kTileY - 1) / kTileY;
-  const int units = tiled_stencil_units(op->nx, op->ny, op->nz, W, &A.zc);
+  A.zc = tiled_stencil_zc(A.tiles_x * A.tiles_y, op->nz, slots);
   A.zchunks = (op->nz + A.zc - 1) / A.zc;
-  const V a[3] = {(V)op->adv[0], (V)op->adv[1], (V)op->adv[2]};
-  A.am0 = op->upw[0] == -1 ? a[0] : V(0);
-  A.ap0 = op->upw[0] == 1 ? a[0] : V(0);
-  A.am1 = op->upw[1] == -1 ? a[1] : V(0);
-  A.ap1 = op->upw[1] == 1 ? a[1] : V(0);
-  A.am2 = op->upw[2] == -1 ? a[2] : V(0);
-  A.ap2 = op->upw[2] == 1 ? a[2] : V(0);
+  A.a0 = (V)op->adv[0];
+  A.a1 = (V)op->adv[1];
+  A.a2 = (V)op->adv[2];
+  A.up0 = op->upw[0] < 0 ? -1 : 1;
+  A.up1 = op->upw[1] < 0 ? -1 : 1;
+  A.up2 = op->upw[2] < 0 ? -1 : 1;
   A.adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
-  return units;
+  return A.tiles_x * A.tiles_y * A.zchunks;
 }
 
 }  // namespace pfk
