@@ -51,8 +51,8 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 # (profiles/pipefcg_pass_96cube.md): one full-window launch (nu = 30) on 96^3,
 # 948.19 MB read + written against 955.51 MB algorithmic, scaled to 128^3 by
 # the number of unknowns.  Valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha256": "134a1f7c9dd91be0e3f4632601cf19bd2ff37bb40af6a4e860eeadf59a135310",
-               "bytes_per_launch": 2.2472e9, "alg_bytes_per_launch": 2.2649e9, "window": 30,
+NCU_TRAFFIC = {"source_sha256": "bfe845324f2509126c3b7d0b6e7eeef16610bd3f8fe3b2d4f41d34b506891369",
+               "bytes_per_launch": 2.2475e9, "alg_bytes_per_launch": 2.2649e9, "window": 30,
                "captured_on": "96^3, scaled by 128^3/96^3"}
 
 

@@ -75,7 +75,8 @@ typedef enum {
   PFK_PIPEGCR = 3,      /* Alg. 11 */
   PFK_FGMRES = 4,       /* Alg. 13 */
   PFK_PIPEFGMRES = 5,   /* Alg. 15 */
-  PFK_PIPEFCG_NAIVE = 6 /* Alg. 7 */
+  PFK_PIPEFCG_NAIVE = 6, /* Alg. 7 */
+  PFK_PIPEGCR_W = 7      /* Alg. 12: w recurred (w_i = w_{i-1} - alpha z_{i-1}), z history */
 } pfk_method;
 
 typedef enum {

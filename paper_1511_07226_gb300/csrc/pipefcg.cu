@@ -1,4 +1,12 @@
-// PIPEFCG (Alg. 8) and naive PIPEFCG (Alg. 7) on one GPU.
+// PIPEFCG (Alg. 8), naive PIPEFCG (Alg. 7) and PIPEGCR_w (Alg. 12) on one GPU.
+//
+// Alg. 12 keeps exactly the vectors of Alg. 8 (x, r, tilde-u, w recurred with
+// z, m = tilde-u + B(w - r), n = A m, and the p, s, q, z histories); what
+// changes is the left operand of every inner product -- w_i instead of
+// tilde-u_i: gamma_i = <r_i, w_i>, delta_i = <w_i, w_i>, beta_{i,k} =
+// -<w_i, s_k>/eta_k -- and the fill's gamma_0 = <r_0, s_0>, eta_0 = <s_0, s_0>
+// (s_0 = A p_0 = w_0, q_0 = B(s_0) = m_0, z_0 = A q_0 = n_0).  The same pass
+// serves both, selecting the left operand per element.
 //
 // One iteration i is three kernel groups, all reading their scalars from the
 // device control block (no host synchronisation, capturable in a CUDA graph):
@@ -47,6 +55,7 @@ struct FcgArgs {
   int64_t N;
   int mmax;
   int naive;
+  int gcrw;          // Alg. 12: inner products against w_i instead of tilde-u_i
   SolveCtl* ctl;
   double* partials;
 };
@@ -128,10 +137,12 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
       a.u[e] = un;
       a.w[e] = wn;
       if (!a.naive) a.t[e] = wn - rn;
-      g0 = fma(un, rn, g0);
-      g1 = fma(un, wn, g1);
+      const double lv = a.gcrw ? wn : un;   // left operand of the inner products
+      g0 = fma(lv, rn, g0);
+      g1 = fma(lv, wn, g1);
       g2 = fma(rn, rn, g2);
-      g3 = fma(un, s, g3);
+      g3 = fma(lv, s, g3);
+      un = lv;
     } else {
 #pragma unroll
       for (int j = 0; j < NW; ++j)
@@ -182,7 +193,8 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
 }
 
 // Pipeline fill dots: gamma_0 = <u_0, r_0>, delta_0 = <u_0, w_0>, ||r_0||^2,
-// then eta_0 = delta_0, alpha_0 = gamma_0 / eta_0 and the fill status.
+// then eta_0 = delta_0, alpha_0 = gamma_0 / eta_0 and the fill status.  For
+// Alg. 12 `u` is w_0 = s_0: gamma_0 = <r_0, s_0>, eta_0 = <s_0, s_0>.
 __global__ void __launch_bounds__(kThreads) pipefcg_fill_dots(const double* __restrict__ u,
                                                               const double* __restrict__ r,
                                                               const double* __restrict__ w, int64_t N,
@@ -225,7 +237,7 @@ int pipefcg_template(int mmax) { return mmax <= 4 ? 4 : mmax <= 8 ? 8 : mmax <= 
 
 class PipeFcg : public Method {
  public:
-  PipeFcg(bool naive) : naive_(naive) {}
+  PipeFcg(bool naive, bool gcrw) : naive_(naive), gcrw_(gcrw) {}
 
   int64_t workspace_doubles(int64_t N, int mmax) const override {
     return 7 * N + 4 * (int64_t)(mmax + 1) * N;
@@ -253,7 +265,7 @@ class PipeFcg : public Method {
     if ((e = op_apply(env.op, m_, n_, nullptr, nullptr, st)) != cudaSuccess) return e;   // n_0 = A m_0
     const int blocks = stream_blocks(env.ctx, N_, 2);
     if (!env.partials_fit(blocks, 3)) return cudaErrorInvalidValue;
-    pipefcg_fill_dots<<<blocks, kThreads, 0, st>>>(u_, r_, w_, N_, env.ctl, env.partials);
+    pipefcg_fill_dots<<<blocks, kThreads, 0, st>>>(gcrw_ ? w_ : u_, r_, w_, N_, env.ctl, env.partials);
     return cudaGetLastError();
   }
 
@@ -261,7 +273,7 @@ class PipeFcg : public Method {
     FcgArgs a;
     a.x = x; a.r = r_; a.u = u_; a.w = w_; a.m = m_; a.n = n_; a.t = t_;
     a.P = P_; a.S = S_; a.Q = Q_; a.Z = Z_;
-    a.N = N_; a.mmax = mmax_; a.naive = naive_ ? 1 : 0;
+    a.N = N_; a.mmax = mmax_; a.naive = naive_ ? 1 : 0; a.gcrw = gcrw_ ? 1 : 0;
     a.ctl = env.ctl; a.partials = env.partials;
     const int tmpl = pipefcg_template(mmax_);
     cudaError_t e = env.mark_pass(0);
@@ -282,6 +294,7 @@ class PipeFcg : public Method {
 
  private:
   bool naive_;
+  bool gcrw_;
   int64_t N_ = 0;
   int mmax_ = 0;
   double *r_ = nullptr, *u_ = nullptr, *w_ = nullptr, *m_ = nullptr, *n_ = nullptr, *t_ = nullptr,
@@ -289,6 +302,7 @@ class PipeFcg : public Method {
   double *P_ = nullptr, *S_ = nullptr, *Q_ = nullptr, *Z_ = nullptr;
 };
 
-Method* make_pipefcg(bool naive) { return new PipeFcg(naive); }
+Method* make_pipefcg(bool naive) { return new PipeFcg(naive, false); }
+Method* make_pipegcr_w() { return new PipeFcg(false, true); }
 
 }  // namespace pfk

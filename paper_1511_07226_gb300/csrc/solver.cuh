@@ -55,6 +55,7 @@ class Method {
 };
 
 Method* make_pipefcg(bool naive);
+Method* make_pipegcr_w();
 Method* make_pipegcr();
 Method* make_pipefgmres(double sigma);
 Method* make_fcg();

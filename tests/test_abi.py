@@ -35,7 +35,7 @@ def test_abi_version(lib):
 @pytest.mark.parametrize("method,mmax,count", [
     ("pipefcg", 30, 4 * 30 + 11), ("fcg", 30, 30 + 6), ("gcr", 30, 2 * 30 + 7),
     ("pipegcr", 30, 2 * 30 + 7 + 30 + 2), ("fgmres", 30, 2 * 30 + 2), ("pipefgmres", 30, 4 * 30 + 2),
-    ("pipefcg", 1, 15)])
+    ("pipefcg", 1, 15), ("pipegcr_w", 30, 4 * 30 + 11)])
 def test_storage_vector_counts_follow_paper(lib, method, mmax, count):
     assert pfk.storage_vectors(method, mmax) == count
 

@@ -1,5 +1,5 @@
-"""PIPEGCR (Alg. 11) and PIPEFGMRES (Alg. 15) on the GPU against the oracle,
-with the envelope protocol of tests/_parity.py."""
+"""PIPEGCR (Alg. 11), PIPEGCR_w (Alg. 12) and PIPEFGMRES (Alg. 15) on the GPU
+against the oracle, with the envelope protocol of tests/_parity.py."""
 import numpy as np
 import pytest
 
@@ -23,33 +23,48 @@ def _problem(dims=(20, 18, 14), contrast=2.0, item=5, vel=(0.0, 0.0, 0.0)):
     return c, O.StencilOperator(c["dims"], c["eta"], vel)
 
 
+@pytest.mark.parametrize("method", ["pipegcr", "pipegcr_w"])
 @pytest.mark.parametrize("pc_kind", ["jacobi", "inner_pcg"])
 @pytest.mark.parametrize("mmax,trunc,norm", [(30, "standard", "natural"), (5, "standard", "unpreconditioned"),
                                              (4, "restart", "natural")])
-def test_pipegcr_stencil(ctx, pc_kind, mmax, trunc, norm):
+def test_pipegcr_stencil(ctx, method, pc_kind, mmax, trunc, norm):
     from paper_1511_07226_gb300 import pfk
     c, aop = _problem()
     mk = (lambda: PC.JacobiPC(aop)) if pc_kind == "jacobi" else (lambda: PC.InnerPCG(aop, 4))
     prm = K.Params(mmax=mmax, rtol=1e-8, truncation=trunc, norm=norm, maxit=600)
-    ref, alts = oracle_with_envelope("pipegcr", aop, mk, c["b"], prm)
+    ref, alts = oracle_with_envelope(method, aop, mk, c["b"], prm)
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
     pc = pfk.Preconditioner(ctx, op, pc_kind, inner_iters=4)
-    x, info, hist = pfk.solve(ctx, op, pc, c["b"], method="pipegcr", mmax=mmax, truncation=trunc, norm=norm,
+    x, info, hist = pfk.solve(ctx, op, pc, c["b"], method=method, mmax=mmax, truncation=trunc, norm=norm,
                               rtol=1e-8, maxit=600, history=4000)
     check_solve(hist, info, ref, alts, rtol=1e-8)
 
 
-def test_pipegcr_csr_nonsymmetric(ctx):
+@pytest.mark.parametrize("method", ["pipegcr", "pipegcr_w"])
+def test_pipegcr_csr_nonsymmetric(ctx, method):
     """CSR storage of an advective (nonsymmetric) stencil: the CR family needs no symmetry."""
     from paper_1511_07226_gb300 import pfk
     c, aop = _problem(dims=(24, 20, 10), contrast=1.0, item=6, vel=(20.0, -10.0, 5.0))
     csr = aop.to_csr()
     prm = K.Params(mmax=20, rtol=1e-8, norm="unpreconditioned", maxit=600)
-    ref, alts = oracle_with_envelope("pipegcr", csr, lambda: PC.JacobiPC(csr), c["b"], prm)
+    ref, alts = oracle_with_envelope(method, csr, lambda: PC.JacobiPC(csr), c["b"], prm)
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"], (20.0, -10.0, 5.0), storage="csr")
-    x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], method="pipegcr", mmax=20,
+    x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], method=method, mmax=20,
                               norm="unpreconditioned", rtol=1e-8, maxit=600, history=4000)
     check_solve(hist, info, ref, alts, rtol=1e-8)
+
+
+def test_pipegcr_w_first_iterations_match_pipegcr(ctx):
+    """Alg. 11 and Alg. 12 differ only in how w_i is obtained (A tilde-u_i versus
+    the recurrence w_{i-1} - alpha z_{i-1}): their first iterations agree up to
+    rounding, on the GPU as in exact arithmetic."""
+    from paper_1511_07226_gb300 import pfk
+    c, aop = _problem(dims=(16, 14, 12), item=7)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "jacobi")
+    _, _, h11 = pfk.solve(ctx, op, pc, c["b"], method="pipegcr", mmax=10, rtol=1e-8, maxit=12, history=20)
+    _, _, h12 = pfk.solve(ctx, op, pc, c["b"], method="pipegcr_w", mmax=10, rtol=1e-8, maxit=12, history=20)
+    assert np.allclose(h12[:8, 0], h11[:8, 0], rtol=1e-9, atol=0.0)
 
 
 @pytest.mark.parametrize("pc_kind,m,sigma", [("jacobi", 30, 1.5), ("inner_pcg", 10, 1.2), ("jacobi", 5, 1.0),
@@ -117,7 +132,7 @@ def test_pipefgmres_breakdown_restarts(ctx):
         assert info["rnorm_true"] <= 1e-8 * info["bnorm"] * (1 + 1e-12)
 
 
-@pytest.mark.parametrize("method", ["fcg", "pipefcg", "gcr", "pipegcr"])
+@pytest.mark.parametrize("method", ["fcg", "pipefcg", "gcr", "pipegcr", "pipegcr_w"])
 def test_true_residual_stagnation_reported(ctx, method):
     """A goal below attainable accuracy ends, as in the oracle, with
     not-converged after max_restarts residual replacements, not with ok."""

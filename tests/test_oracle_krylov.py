@@ -331,7 +331,7 @@ def test_sigma_estimate_approaches_largest_eigenvalue():
     assert K.estimate_sigma(op, PC.JacobiPC(op), b) <= lam * (1 + 1e-12)
 
 
-@pytest.mark.parametrize("method", ["fcg", "pipefcg", "gcr", "pipegcr"])
+@pytest.mark.parametrize("method", ["fcg", "pipefcg", "gcr", "pipegcr", "pipegcr_w"])
 def test_true_residual_stagnation_is_not_convergence(method):
     """A goal below the attainable accuracy: the recurred residual keeps falling
     but ||b - A x|| stalls at rounding level, so after max_restarts residual
