@@ -83,7 +83,8 @@ typedef enum {
   PFK_PC_NONE = 0,       /* B(v) = v */
   PFK_PC_JACOBI = 1,     /* B(v) = D^-1 v */
   PFK_PC_INNER_PCG = 2,  /* inner_iters iterations of Jacobi-PCG (Alg. 3, M^-1 = D^-1) from 0 */
-  PFK_PC_CHEBYSHEV = 3   /* inner_iters Chebyshev-Jacobi sweeps from 0 */
+  PFK_PC_CHEBYSHEV = 3,  /* inner_iters Chebyshev-Jacobi sweeps from 0 */
+  PFK_PC_NOISY = 4       /* B(r) = r + eta ||r|| xi_j / ||xi_j|| (pfk_create_noisy_preconditioner) */
 } pfk_pc_kind;
 
 typedef enum {
@@ -188,6 +189,15 @@ typedef struct {
 
 pfk_status pfk_create_preconditioner(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc* desc,
                                      pfk_pc** pc);
+/* The preconditioner of the paper's toy experiment (Sec. 3.2, Fig. FCGtoy):
+ * B(r) = r + eta ||r||_2 xi_j / ||xi_j||_2, where xi_j is row (j mod count) of
+ * `bank` (count x n doubles, row-major; host or device per bank_on_device; copied
+ * at creation) and j counts this preconditioner's applications since its
+ * creation (j = 0 first).  The noise is an input, so a CPU reference drawing the
+ * same rows reproduces the sequence.  Works with any operator.  Errors:
+ * PFK_ERR_INVALID (eta < 0, count < 1, a zero bank row), PFK_ERR_OOM, PFK_ERR_CUDA. */
+pfk_status pfk_create_noisy_preconditioner(pfk_context* ctx, const pfk_operator* op, double eta, const double* bank,
+                                           int count, int bank_on_device, pfk_pc** pc);
 pfk_status pfk_destroy_preconditioner(pfk_pc* pc);
 /* y = B(v); device pointers of length n, must not overlap. */
 pfk_status pfk_pc_apply(pfk_context* ctx, const pfk_pc* pc, const double* v, double* y);

@@ -12,6 +12,8 @@ namespace pfk {
 pfk_status create_stencil(pfk_context* ctx, const pfk_operator_desc* desc, pfk_operator* op);
 pfk_status create_csr(pfk_context* ctx, const pfk_operator_desc* desc, pfk_operator* op);
 pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc* desc, pfk_pc* pc);
+pfk_status create_noisy_pc(pfk_context* ctx, const pfk_operator* op, double eta, const double* bank, int count,
+                           int bank_on_device, pfk_pc* pc);
 pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, const pfk_solve_params* prm,
                      const double* b, double* x, pfk_solve_info* info);
 pfk_status solve_workspace_bytes(int method, int mmax, int64_t n, int64_t* bytes);
@@ -205,6 +207,25 @@ pfk_status pfk_create_preconditioner(pfk_context* ctx, const pfk_operator* op, c
   return PFK_OK;
 }
 
+pfk_status pfk_create_noisy_preconditioner(pfk_context* ctx, const pfk_operator* op, double eta, const double* bank,
+                                           int count, int bank_on_device, pfk_pc** out) {
+  CHECK_ARG(ctx, ctx && op && bank && out, "NULL argument");
+  CHECK_ARG(ctx, eta >= 0.0 && count >= 1, "noisy preconditioner needs eta >= 0 and count >= 1");
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  pfk_pc* pc = new (std::nothrow) pfk_pc();
+  if (!pc) return PFK_ERR_OOM;
+  pc->device = ctx->device;
+  pc->stream = ctx->stream;
+  pfk_status s = create_noisy_pc(ctx, op, eta, bank, count, bank_on_device, pc);
+  if (s != PFK_OK) {
+    pfk_destroy_preconditioner(pc);
+    return s;
+  }
+  *out = pc;
+  return PFK_OK;
+}
+
 pfk_status pfk_destroy_preconditioner(pfk_pc* pc) {
   if (!pc) return PFK_OK;
   // as for operators: never dereference the (possibly destroyed) context
@@ -213,6 +234,8 @@ pfk_status pfk_destroy_preconditioner(pfk_pc* pc) {
   if (pc->buf) cudaFreeAsync(pc->buf, pc->stream);
   if (pc->ctl) cudaFreeAsync(pc->ctl, pc->stream);
   if (pc->partials) cudaFreeAsync(pc->partials, pc->stream);
+  if (pc->bank) cudaFreeAsync(pc->bank, pc->stream);
+  if (pc->bank_inv_norm) cudaFreeAsync(pc->bank_inv_norm, pc->stream);
   cudaStreamSynchronize(pc->stream);
   delete pc;
   return PFK_OK;

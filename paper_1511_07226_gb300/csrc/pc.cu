@@ -71,6 +71,63 @@ __global__ void __launch_bounds__(kThreads) jacobi_kernel(const double* __restri
 }
 
 // ---------------------------------------------------------------------------
+// Noisy preconditioner (toy experiment, Fig. FCGtoy)
+// ---------------------------------------------------------------------------
+
+// ||v||; the last block picks the bank row j = calls mod count, the scale
+// eta ||v|| / ||xi_j|| and advances the application counter.
+__global__ void __launch_bounds__(kThreads) noisy_norm_kernel(const double* __restrict__ v, int64_t n, double eta,
+                                                              const double* __restrict__ inv_norm, int count,
+                                                              PcCtl* ctl, double* partials,
+                                                              const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  double acc[1] = {0.0};
+  GRID_LOOP(c, n) acc[0] = fma(v[c], v[c], acc[0]);
+  __shared__ double smem[kThreads / 32];
+  __shared__ double sums[1];
+  if (reduce_last_block<1>(acc, 1, partials, 1, &ctl->counter, smem, sums) && threadIdx.x == 0) {
+    const long long j = ctl->calls % count;
+    ctl->row = j;
+    ctl->scale = eta * sqrt(sums[0]) * inv_norm[j];
+    ctl->calls += 1;
+  }
+}
+
+// out = add + v + scale xi_row
+__global__ void __launch_bounds__(kThreads) noisy_apply_kernel(const double* __restrict__ v,
+                                                               const double* __restrict__ bank, int64_t n,
+                                                               const PcCtl* ctl, const double* __restrict__ add,
+                                                               double* __restrict__ out,
+                                                               const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  const double s = ctl->scale;
+  const double* xi = bank + (size_t)ctl->row * (size_t)n;
+  GRID_LOOP(c, n) {
+    const double y = fma(s, xi[c], v[c]);
+    out[c] = add ? add[c] + y : y;
+  }
+}
+
+// 1 / ||xi_j|| for every bank row (one block per row, fixed order).
+__global__ void __launch_bounds__(kThreads) noisy_row_norms_kernel(const double* __restrict__ bank, int64_t n,
+                                                                   double* __restrict__ inv_norm,
+                                                                   int* __restrict__ bad) {
+  const double* xi = bank + (size_t)blockIdx.x * (size_t)n;
+  double acc = 0.0;
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) acc = fma(xi[c], xi[c], acc);
+  __shared__ double sm[kThreads / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w];
+    if (!(s > 0.0)) atomicExch(bad, 1);
+    inv_norm[blockIdx.x] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Inner Jacobi-PCG
 // ---------------------------------------------------------------------------
 
@@ -351,6 +408,14 @@ cudaError_t pc_apply(const pfk_pc* pc, const double* v, double* out, const doubl
     jacobi_kernel<<<stream_blocks(pc->ctx, n, 8), kThreads, 0, st>>>(dinv, v, add, out, n, status);
     return cudaGetLastError();
   }
+  if (pc->kind == PFK_PC_NOISY) {
+    const int blocks = stream_blocks(pc->ctx, n, 2);
+    noisy_norm_kernel<<<blocks, kThreads, 0, st>>>(v, n, pc->noise_eta, pc->bank_inv_norm, pc->bank_count, pc->ctl,
+                                                   pc->partials, status);
+    noisy_apply_kernel<<<stream_blocks(pc->ctx, n, 8), kThreads, 0, st>>>(v, pc->bank, n, pc->ctl, add, out,
+                                                                          status);
+    return cudaGetLastError();
+  }
   if (pc->kind == PFK_PC_INNER_PCG) {
     if (pc->precision == PFK_FP64)
       return inner_pcg<double, double>(pc, make_stencil<double, double>(op, op->d, op->kx, op->ky, op->kz, op->dinv),
@@ -374,6 +439,38 @@ cudaError_t pc_apply(const pfk_pc* pc, const double* v, double* out, const doubl
                                          v, out, add, status, st);
 }
 
+pfk_status create_noisy_pc(pfk_context* ctx, const pfk_operator* op, double eta, const double* bank, int count,
+                           int bank_on_device, pfk_pc* pc) {
+  pc->ctx = ctx;
+  pc->op = op;
+  pc->kind = PFK_PC_NOISY;
+  pc->noise_eta = eta;
+  pc->bank_count = count;
+  const int64_t n = op->n;
+  cudaStream_t st = ctx->stream;
+  const size_t bytes = (size_t)count * (size_t)n * sizeof(double);
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->bank, bytes, st));
+  PFK_CUDA(ctx, cudaMemcpyAsync(pc->bank, bank, bytes, bank_on_device ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyHostToDevice, st));
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->bank_inv_norm, (size_t)count * sizeof(double) + sizeof(int), st));
+  int* bad = (int*)(pc->bank_inv_norm + count);
+  PFK_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), st));
+  noisy_row_norms_kernel<<<count, kThreads, 0, st>>>(pc->bank, n, pc->bank_inv_norm, bad);
+  PFK_CUDA(ctx, cudaGetLastError());
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->ctl, sizeof(PcCtl), st));
+  PFK_CUDA(ctx, cudaMemsetAsync(pc->ctl, 0, sizeof(PcCtl), st));
+  pc->partials_cap = ctx->num_sms * 8;
+  PFK_CUDA(ctx, cudaMallocAsync((void**)&pc->partials, (size_t)pc->partials_cap * sizeof(double), st));
+  int hbad = 0;
+  PFK_CUDA(ctx, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PFK_CUDA(ctx, cudaStreamSynchronize(st));
+  if (hbad) {
+    set_error(ctx, "a noise bank row has zero norm");
+    return PFK_ERR_INVALID;
+  }
+  return PFK_OK;
+}
+
 pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc* desc, pfk_pc* pc) {
   pc->ctx = ctx;
   pc->op = op;
@@ -381,7 +478,7 @@ pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc
   pc->inner = desc->inner_iters;
   pc->precision = desc->precision;
   const bool stencil = op->d != nullptr;
-  if (pc->kind < PFK_PC_NONE || pc->kind > PFK_PC_CHEBYSHEV) {
+  if (pc->kind < PFK_PC_NONE || pc->kind > PFK_PC_CHEBYSHEV) {   // PFK_PC_NOISY has its own constructor
     set_error(ctx, "unknown preconditioner kind");
     return PFK_ERR_INVALID;
   }

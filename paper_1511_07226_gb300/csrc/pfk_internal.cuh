@@ -73,6 +73,9 @@ struct PcCtl {
   double beta[64];
   unsigned int counter;
   unsigned int pad1;
+  long long calls;         // noisy preconditioner: applications so far
+  double scale;            // noisy preconditioner: eta ||v|| / ||xi_j|| of the current application
+  long long row;           // noisy preconditioner: j mod count of the current application
 };
 
 }  // namespace pfk
@@ -150,6 +153,11 @@ struct pfk_pc {
   pfk::PcCtl* ctl = nullptr;
   double* partials = nullptr;
   int partials_cap = 0;         // doubles in `partials` (bounds the grid of the reduction kernels)
+  // noisy preconditioner: the noise bank (count x n) and 1 / ||xi_j||
+  double noise_eta = 0.0;
+  double* bank = nullptr;
+  double* bank_inv_norm = nullptr;
+  int bank_count = 0;
 };
 
 namespace pfk {

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "oom", -3: "cuda", -4:
                 -5: "not_converged", -6: "timeout", -7: "cancelled", -8: "busy"}
 METHODS = {"fcg": 0, "pipefcg": 1, "gcr": 2, "pipegcr": 3, "fgmres": 4, "pipefgmres": 5, "pipefcg_naive": 6,
            "pipegcr_w": 7}
-PC_KINDS = {"none": 0, "jacobi": 1, "inner_pcg": 2, "chebyshev": 3}
+PC_KINDS = {"none": 0, "jacobi": 1, "inner_pcg": 2, "chebyshev": 3, "noisy": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 OP_KINDS = {"stencil2d": 0, "stencil3d": 1, "csr": 2}
 STORAGE = {"matrix_free": 0, "csr": 1}
@@ -88,6 +88,8 @@ _SIGS = {
     "pfk_operator_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pfk_create_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(PcDesc), C.POINTER(C.c_void_p)]),
     "pfk_destroy_preconditioner": (C.c_int, [C.c_void_p]),
+    "pfk_create_noisy_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int, C.c_int,
+                                                  C.POINTER(C.c_void_p)]),
     "pfk_pc_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pfk_default_params": (C.c_int, [C.POINTER(SolveParams)]),
     "pfk_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p,
@@ -266,6 +268,20 @@ class Preconditioner:
         _check(load().pfk_create_preconditioner(ctx.h, op.h, C.byref(d), C.byref(h)), ctx.h)
         self.h = h
         self.kind, self.precision = kind, precision
+
+    @classmethod
+    def noisy(cls, ctx: Context, op: Operator, eta: float, bank):
+        """B(r) = r + eta ||r|| xi_j / ||xi_j||, xi_j = row j mod count of `bank` (the toy experiment's
+        preconditioner); j counts applications since creation."""
+        bk = np.ascontiguousarray(bank, dtype=np.float64)
+        self = cls.__new__(cls)
+        self.ctx, self.op = ctx, op
+        h = C.c_void_p()
+        _check(load().pfk_create_noisy_preconditioner(ctx.h, op.h, float(eta), C.c_void_p(bk.ctypes.data),
+                                                      int(bk.shape[0]), 0, C.byref(h)), ctx.h)
+        self.h = h
+        self.kind, self.precision = "noisy", "fp64"
+        return self
 
     def apply(self, v):
         torch = _torch()
