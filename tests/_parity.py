@@ -8,8 +8,11 @@ summation order of its inner products, shows the size of that drift.  The
 protocol is therefore:
 
 1. Envelope: the oracle is re-run with three other summation orders of every
-   inner product (pairwise, reversed, exactly rounded via math.fsum); env_i is
-   the running maximum over those runs of |rho_alt - rho| / rho at entry i.
+   inner product (pairwise, reversed, exactly rounded via math.fsum) and, for
+   a stencil operator, once more with the operator applied in row-sum form
+   (its assembled CSR: d_i u_i - sum K u_nbr, the form the GPU evaluates)
+   instead of the flux form sum K (u_i - u_nbr); env_i is the running maximum
+   over those runs of |rho_alt - rho| / rho at entry i.
 2. Strict prefix: on every entry where env_i <= 1e-11 the GPU must agree with
    the oracle to 1e-10 relative.
 3. Envelope region: while env_i <= 1e-4 (the trajectories are still
@@ -63,6 +66,8 @@ def oracle_with_envelope(method, A, make_B, b, prm, x0=None):
             alts.append(K.solve(method, A, make_B(), b, x0=x0, prm=prm))
     finally:
         K.dot, PC._dot = saved
+    if hasattr(A, "to_csr"):
+        alts.append(K.solve(method, A.to_csr(), make_B(), b, x0=x0, prm=prm))
     return ref, alts
 
 
