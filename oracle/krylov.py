@@ -339,11 +339,14 @@ def cgfcg(A, B, b, x0, prm: Params) -> Result:
             alpha = gamma / eta[i]
 
 
-def pipefcg(A, B, b, x0, prm: Params, naive: bool = False) -> Result:
+def pipefcg(A, B, b, x0, prm: Params, naive: bool = False, theta: bool = False) -> Result:
     """Pipelined FCG, Alg. 8; ``naive=True`` gives Alg. 7 (m_i = B(w_i)).
 
     The only difference between the two is the pipelined preconditioner input:
     Alg. 8 applies B to w_i - r_i and adds tilde-u_i back (eq. BwMinusR).
+    ``theta=True`` is the projection repair of eq. (proj) in Alg. 8's
+    indexing: m_i = theta_i tilde-u_i + B(w_i - theta_i r_i) with
+    theta_i = <r_i, w_i> / <r_i, r_i>; theta = 1 gives Alg. 8, theta = 0 Alg. 7.
     """
     res = Result(x=x0.copy())
     mon = _Monitor(A, b, prm, res)
@@ -394,6 +397,9 @@ def pipefcg(A, B, b, x0, prm: Params, naive: bool = False) -> Result:
                 break
             if naive:
                 m = B(w)
+            elif theta:
+                th = dot(r, w) / dot(r, r)
+                m = th * u + B(w - th * r)
             else:
                 m = u + B(w - r)
             n = A(m)
@@ -744,6 +750,7 @@ def pipefgmres(A, B, b, x0, prm: Params) -> Result:
 METHODS = {
     "pcg": pcg, "fcg": fcg, "cgfcg": cgfcg, "pipefcg": pipefcg,
     "pipefcg_naive": lambda A, B, b, x0, prm: pipefcg(A, B, b, x0, prm, naive=True),
+    "pipefcg_theta": lambda A, B, b, x0, prm: pipefcg(A, B, b, x0, prm, theta=True),
     "gcr": gcr, "pipegcr": pipegcr, "pipegcr_w": pipegcr_w,
     "fgmres": fgmres, "cgfgmres": cgfgmres, "pipefgmres": pipefgmres,
 }

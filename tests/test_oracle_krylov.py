@@ -346,3 +346,50 @@ def test_true_residual_stagnation_is_not_convergence(method):
     # with an attainable goal the same solve converges
     r2 = K.solve(method, A, PC.JacobiPC(A), c["b"], prm=K.Params(mmax=10, rtol=1e-10, max_restarts=2))
     assert r2.status == "converged" and r2.rnorm_true <= 1e-10 * r2.bnorm
+
+
+def test_theta_projection_reduces_to_alg8_and_alg7():
+    """eq. (proj): m_i = theta tilde-u_i + B(w_i - theta r_i).  With a linear B
+    every theta gives B(w_i) + theta (tilde-u_i - B(r_i)) = B(w_i) (tilde-u_i =
+    B(r_i) in exact arithmetic), so the theta variant equals Alg. 8 and CG; and
+    the computed theta_i is <r_i, w_i> / <r_i, r_i> of the run's own vectors."""
+    a, A, b = _spd_system(n=30, cond=30.0, item=11)
+    prm = K.Params(rtol=0.0, mmax=30, maxit=12, trace=True)
+    r8 = K.pipefcg(A, PC.JacobiPC(A), b, np.zeros_like(b), prm)
+    rt = K.pipefcg(A, PC.JacobiPC(A), b, np.zeros_like(b), prm, theta=True)
+    xs = np.linalg.solve(a, b)
+    for t8, tt in zip(r8.trace, rt.trace):
+        assert np.linalg.norm(tt["x"] - t8["x"]) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_theta_projection_with_nonlinear_b():
+    """With the noisy B of Fig. FCGtoy (B ~ I) the theta variant converges like
+    Alg. 8, unlike Alg. 7; theta_i = <r_i, A tilde-u_i> / <r_i, r_i> is then a
+    Rayleigh quotient of A (eigenvalues 1..5), not 1 (theta tends to 1 only as
+    B tends to A^-1)."""
+    t = W.toy_diagonal()
+    A = O.DiagonalOperator(t["diag"])
+    xs = t["b"] / t["diag"]
+    bank = W.noise_bank(100, 500, seed_item=7)
+    r = K.solve("pipefcg_theta", A, PC.NoisyPC(1e-3, bank), t["b"],
+                prm=K.Params(mmax=32, rtol=0.0, maxit=60, true_residual_check=False, trace=True))
+    err = min(np.linalg.norm(tr["x"] - xs) / np.linalg.norm(xs) for tr in r.trace)
+    assert err <= 1e-6
+    for tr in r.trace[:10]:
+        th = (tr["r"] @ tr["w"]) / (tr["r"] @ tr["r"])
+        assert 0.9 < th < 5.1
+
+
+def test_theta_projection_step_replay():
+    """Each m_i of the theta variant with a deterministic nonlinear B (inner PCG)
+    equals theta_i tilde-u_i + B(w_i - theta_i r_i), theta_i = <r_i, w_i> / <r_i, r_i>
+    recomputed from the trace; a wrong theta (e.g. 1, or <r, w> / <w, w>) fails."""
+    op, b = _stencil_problem(item=12)
+    B = PC.InnerPCG(op, 2)
+    r = K.solve("pipefcg_theta", op, B, b, prm=K.Params(rtol=0.0, mmax=10, maxit=8, trace=True))
+    for tr in r.trace[1:]:
+        th = float(np.dot(tr["r"], tr["w"]) / np.dot(tr["r"], tr["r"]))
+        m = th * tr["u"] + PC.InnerPCG(op, 2)(tr["w"] - th * tr["r"])
+        assert np.linalg.norm(m - tr["m"]) <= 1e-12 * np.linalg.norm(m)
+        m1 = tr["u"] + PC.InnerPCG(op, 2)(tr["w"] - tr["r"])
+        assert np.linalg.norm(m1 - tr["m"]) > 1e-6 * np.linalg.norm(m)
