@@ -232,8 +232,9 @@ def main():
     ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase"],
                     help="--ncu-case problem: Gaussian-field Poisson (4 inner PCG) or two-phase advection "
                          "(8 Chebyshev sweeps)")
-    ap.add_argument("--extras", default="fcg,pipegcr,batched,fgmres256,serve",
-                    help="comma-separated secondary measurements (fcg, pipegcr, batched, fgmres256, serve) or 'none'")
+    ap.add_argument("--extras", default="fcg,pipegcr,nu_sweep,batched,fgmres256,serve",
+                    help="comma-separated secondary measurements (fcg, pipegcr, nu_sweep, batched, fgmres256, "
+                         "serve) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
@@ -446,6 +447,31 @@ def extra_fcg(ctx, dev, args) -> dict:
             "true_rel_residual": info["rnorm_true"] / info["bnorm"], "restarts": info["restarts"]}
 
 
+def extra_nu_sweep(ctx, dev, args) -> dict:
+    """PIPEFCG on the 128^3 problem for nu_max = 1 (IPCG), 5, 10, 30, standard and
+    restart-style truncation (Sec. 5 remark), and the eq. (proj) theta variant:
+    time to 1e-8, iterations, time per iteration."""
+    import torch
+    from paper_1511_07226_gb300 import pfk
+    c = make_problem()
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4, precision="fp64")
+    b = torch.from_numpy(c["b"]).to(dev)
+    out = []
+    cases = [("pipefcg", 1, "standard"), ("pipefcg", 5, "standard"), ("pipefcg", 10, "standard"),
+             ("pipefcg", 30, "standard"), ("pipefcg", 30, "restart"), ("pipefcg_theta", 30, "standard")]
+    for method, nu, trunc in cases:
+        x = torch.zeros_like(b)
+        _, info, _ = pfk.solve(ctx, op, pc, b, x0=x, method=method, mmax=nu, truncation=trunc, rtol=1e-8,
+                               maxit=NU_SWEEP_MAXIT, max_restarts=MAX_RESTARTS)
+        out.append({"method": method, "nu_max": nu, "truncation": trunc, "status": info["status_name"],
+                    "iterations": info["iterations"], "restarts": info["restarts"],
+                    "time_ms": info["time_ms"], "ms_per_iteration": info["time_ms"] / max(info["iterations"], 1),
+                    "true_rel_residual": info["rnorm_true"] / info["bnorm"]})
+    return {"workload": "128^3 contrast 1e6, 4 inner Jacobi-PCG (FP64), rtol 1e-8, "
+                        f"at most {NU_SWEEP_MAXIT} iterations", "runs": out}
+
+
 def extra_batched(ctx, dev, args) -> dict:
     """512 independent 2D systems (sides 32..256) in one persistent PIPEFCG launch."""
     import workloads as W
@@ -550,8 +576,9 @@ def extra_serve(ctx, dev, args) -> dict:
 MAX_RESTARTS = 200
 FGMRES256_ITERS = 900
 BATCHED_MAXIT = 4000
+NU_SWEEP_MAXIT = 4000
 
-EXTRAS = {"fcg": extra_fcg, "pipegcr": extra_pipegcr, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
+EXTRAS = {"fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
 
 
 # Iterations of one 128^3 solve for the reference arm's extrapolation: the

@@ -76,7 +76,9 @@ typedef enum {
   PFK_FGMRES = 4,       /* Alg. 13 */
   PFK_PIPEFGMRES = 5,   /* Alg. 15 */
   PFK_PIPEFCG_NAIVE = 6, /* Alg. 7 */
-  PFK_PIPEGCR_W = 7      /* Alg. 12: w recurred (w_i = w_{i-1} - alpha z_{i-1}), z history */
+  PFK_PIPEGCR_W = 7,     /* Alg. 12: w recurred (w_i = w_{i-1} - alpha z_{i-1}), z history */
+  PFK_PIPEFCG_THETA = 8  /* Alg. 8 with the projection repair of eq. (proj):
+                            m_i = theta_i u_i + B(w_i - theta_i r_i), theta_i = <r_i, w_i>/<r_i, r_i> */
 } pfk_method;
 
 typedef enum {

@@ -277,7 +277,8 @@ int pfk_method_storage_vectors(int method, int mmax) {
   switch (method) {
     case PFK_PIPEFCG:
     case PFK_PIPEFCG_NAIVE:
-    case PFK_PIPEGCR_W: return 4 * mmax + 11;
+    case PFK_PIPEGCR_W:
+    case PFK_PIPEFCG_THETA: return 4 * mmax + 11;
     case PFK_FCG: return mmax + 6;
     case PFK_GCR: return 2 * mmax + 7;
     case PFK_PIPEGCR: return 2 * mmax + 7 + mmax + 2;

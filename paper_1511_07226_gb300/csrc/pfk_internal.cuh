@@ -61,6 +61,7 @@ struct SolveCtl {
   int passes;              // fused passes that did work
   double alg_bytes;        // their algorithmic HBM bytes
   double alg_flops;        // their FP64 flops (FMA = 2)
+  double theta;            // projection coefficient <r_i, w_i>/<r_i, r_i> (eq. proj variant)
 };
 
 // Control block of a preconditioner application (inner iterations).

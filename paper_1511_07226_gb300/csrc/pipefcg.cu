@@ -8,6 +8,12 @@
 // (s_0 = A p_0 = w_0, q_0 = B(s_0) = m_0, z_0 = A q_0 = n_0).  The same pass
 // serves both, selecting the left operand per element.
 //
+// The projection repair of eq. (proj) (theta variant) adds <r_i, w_i> to the
+// pass's reduction; the scalar phase forms theta_i = <r_i, w_i>/<r_i, r_i> and a
+// small kernel writes the preconditioner input t = w_i - theta_i r_i and
+// theta_i u_i (added back by the preconditioner's epilogue).  On one GPU the
+// extra inner product rides on the pass's reduction; nothing blocks.
+//
 // One iteration i is three kernel groups, all reading their scalars from the
 // device control block (no host synchronisation, capturable in a CUDA graph):
 //
@@ -56,6 +62,7 @@ struct FcgArgs {
   int mmax;
   int naive;
   int gcrw;          // Alg. 12: inner products against w_i instead of tilde-u_i
+  int theta;         // eq. (proj): also <r_i, w_i>; t is written by theta_prep_kernel
   SolveCtl* ctl;
   double* partials;
 };
@@ -71,13 +78,13 @@ constexpr int kPassThreads = 128;
 constexpr int kPassBlocksPerSm = 6;
 constexpr int kSkStride = kPassThreads + 1;   // padding: conflict-free row reads
 static_assert(kPassBlocksPerSm <= kMaxBlocksPerSm, "partials are sized for kMaxBlocksPerSm blocks per SM");
-static_assert(PFK_MAX_MMAX + 4 <= kPartialStride, "partials are sized for kPartialStride values per block");
+static_assert(PFK_MAX_MMAX + 5 <= kPartialStride, "partials are sized for kPartialStride values per block");
 
 template <int NW>
 __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(FcgArgs a) {
   SolveCtl* ctl = a.ctl;
   if (ctl->status != kRun) return;
-  constexpr int ND = NW + 4;
+  constexpr int ND = NW + 5;
   constexpr int NWARPS = kPassThreads / 32;
   __shared__ double s_beta[NW];
   __shared__ size_t s_off[NW];
@@ -102,8 +109,9 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
   const double* warp_u = s_u + warp * 32;
   const double* lane_row = s_sk + lane * kSkStride + warp * 32;
 
-  // per-thread sums of gamma, delta, ||r||^2, <u, s_{i-1}>; lane-owned window sum
-  double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0, gw = 0.0;
+  // per-thread sums of gamma, delta, ||r||^2, <u, s_{i-1}>, <r, w> (theta
+  // variant); lane-owned window sum
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0, g4 = 0.0, gw = 0.0;
 
   for (int64_t base = (int64_t)blockIdx.x * kPassThreads; base < N; base += (int64_t)gridDim.x * kPassThreads) {
     const int64_t e = base + threadIdx.x;
@@ -136,7 +144,8 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
       a.r[e] = rn;
       a.u[e] = un;
       a.w[e] = wn;
-      if (!a.naive) a.t[e] = wn - rn;
+      if (!a.naive && !a.theta) a.t[e] = wn - rn;
+      if (a.theta) g4 = fma(rn, wn, g4);
       const double lv = a.gcrw ? wn : un;   // left operand of the inner products
       g0 = fma(lv, rn, g0);
       g1 = fma(lv, wn, g1);
@@ -162,17 +171,21 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
   // block partials: scalars by warp reduction, window sums straight from their lanes
   {
     const double w0 = warp_sum(g0), w1 = warp_sum(g1), w2 = warp_sum(g2), w3 = warp_sum(g3);
-    const int nd = nwp + 4;
+    const int nd = nwp + 4 + (a.theta ? 1 : 0);
     if (lane == 0) {
       s_red[warp * nd + 0] = w0;
       s_red[warp * nd + 1] = w1;
       s_red[warp * nd + 2] = w2;
       s_red[warp * nd + 3] = w3;
     }
+    if (a.theta) {
+      const double w4 = warp_sum(g4);
+      if (lane == 0) s_red[warp * nd + 4 + nwp] = w4;
+    }
     if (lane < nwp) s_red[warp * nd + 4 + lane] = gw;
     __syncthreads();
   }
-  if (!combine_block_partials(s_red, nwp + 4, a.partials, ND, &ctl->counter, s_sum)) return;
+  if (!combine_block_partials(s_red, nwp + 4 + (a.theta ? 1 : 0), a.partials, ND, &ctl->counter, s_sum)) return;
   if (threadIdx.x != 0) return;
 
   // ---- scalar phase of iteration i (one thread) ----
@@ -182,8 +195,9 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
   // vectors read; p, s, q, z, x, r, u, w (and t) written.  FP64 flops: 4 nu
   // MAXPY FMAs, 4 advance FMAs, nu + 4 dot FMAs, and the subtraction for t.
   ctl->passes += 1;
-  ctl->alg_bytes += 8.0 * (double)N * (double)(4 * nwp + 14 + (a.naive ? 0 : 1));
-  ctl->alg_flops += (double)N * (2.0 * (5 * nwp + 8) + (a.naive ? 0.0 : 1.0));
+  ctl->alg_bytes += 8.0 * (double)N * (double)(4 * nwp + 14 + ((a.naive || a.theta) ? 0 : 1));
+  ctl->alg_flops += (double)N * (2.0 * (5 * nwp + 8 + (a.theta ? 1 : 0)) + ((a.naive || a.theta) ? 0.0 : 1.0));
+  if (a.theta) ctl->theta = rr > 0.0 ? s_sum[4 + nwp] / rr : 1.0;
   const int nu = nu_window(i, a.mmax, ctl->truncation);
   // window dots in order k = i-1-nwp .. i-1 (W_{i-1}, then s_{i-1}); W_i is
   // the last nu of them
@@ -214,6 +228,20 @@ __global__ void __launch_bounds__(kThreads) pipefcg_fill_dots(const double* __re
   cgcr_fill_scalars(ctl, s_sum[0], s_sum[1], s_sum[2]);
 }
 
+// eq. (proj) variant: t = w - theta r and tu = theta u (the preconditioner adds tu).
+__global__ void __launch_bounds__(kThreads) theta_prep_kernel(const double* __restrict__ w,
+                                                              const double* __restrict__ r,
+                                                              const double* __restrict__ u, double* __restrict__ t,
+                                                              double* __restrict__ tu, int64_t N,
+                                                              const SolveCtl* ctl) {
+  if (ctl->status != kRun) return;
+  const double th = ctl->theta;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    t[e] = fma(-th, r[e], w[e]);
+    tu[e] = th * u[e];
+  }
+}
+
 template <int NW>
 static cudaError_t launch_pass(const FcgArgs& a, int blocks, cudaStream_t st) {
   pipefcg_pass<NW><<<blocks, kPassThreads, 0, st>>>(a);
@@ -237,7 +265,7 @@ int pipefcg_template(int mmax) { return mmax <= 4 ? 4 : mmax <= 8 ? 8 : mmax <= 
 
 class PipeFcg : public Method {
  public:
-  PipeFcg(bool naive, bool gcrw) : naive_(naive), gcrw_(gcrw) {}
+  PipeFcg(bool naive, bool gcrw, bool theta = false) : naive_(naive), gcrw_(gcrw), theta_(theta) {}
 
   int64_t workspace_doubles(int64_t N, int mmax) const override {
     return 7 * N + 4 * (int64_t)(mmax + 1) * N;
@@ -273,7 +301,7 @@ class PipeFcg : public Method {
     FcgArgs a;
     a.x = x; a.r = r_; a.u = u_; a.w = w_; a.m = m_; a.n = n_; a.t = t_;
     a.P = P_; a.S = S_; a.Q = Q_; a.Z = Z_;
-    a.N = N_; a.mmax = mmax_; a.naive = naive_ ? 1 : 0; a.gcrw = gcrw_ ? 1 : 0;
+    a.N = N_; a.mmax = mmax_; a.naive = naive_ ? 1 : 0; a.gcrw = gcrw_ ? 1 : 0; a.theta = theta_ ? 1 : 0;
     a.ctl = env.ctl; a.partials = env.partials;
     const int tmpl = pipefcg_template(mmax_);
     cudaError_t e = env.mark_pass(0);
@@ -281,13 +309,20 @@ class PipeFcg : public Method {
     const int64_t need = (N_ + kPassThreads - 1) / kPassThreads;
     const int64_t cap = (int64_t)env.ctx->num_sms * kPassBlocksPerSm;
     const int blocks = (int)(need < cap ? need : cap);
-    if (!env.partials_fit(blocks, tmpl + 4)) return cudaErrorInvalidValue;
+    if (!env.partials_fit(blocks, tmpl + 5)) return cudaErrorInvalidValue;
     e = launch_pass_any(a, tmpl, blocks, env.st);
     if (e != cudaSuccess) return e;
     if ((e = env.mark_pass(1)) != cudaSuccess) return e;
     const int* status = &env.ctl->status;
-    if (naive_) e = env.pc_apply(w_, m_, nullptr, status);      // m_i = B(w_i)          (Alg. 7)
-    else e = env.pc_apply(t_, m_, u_, status);                   // m_i = u_i + B(w_i - r_i) (Alg. 8)
+    if (naive_) {
+      e = env.pc_apply(w_, m_, nullptr, status);                 // m_i = B(w_i)          (Alg. 7)
+    } else if (theta_) {
+      theta_prep_kernel<<<stream_blocks(env.ctx, N_, 8), kThreads, 0, env.st>>>(w_, r_, u_, t_, tmp_, N_, env.ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      e = env.pc_apply(t_, m_, tmp_, status);                    // m_i = theta u_i + B(w_i - theta r_i)
+    } else {
+      e = env.pc_apply(t_, m_, u_, status);                      // m_i = u_i + B(w_i - r_i) (Alg. 8)
+    }
     if (e != cudaSuccess) return e;
     return op_apply(env.op, m_, n_, nullptr, status, env.st);    // n_i = A m_i
   }
@@ -295,6 +330,7 @@ class PipeFcg : public Method {
  private:
   bool naive_;
   bool gcrw_;
+  bool theta_;
   int64_t N_ = 0;
   int mmax_ = 0;
   double *r_ = nullptr, *u_ = nullptr, *w_ = nullptr, *m_ = nullptr, *n_ = nullptr, *t_ = nullptr,
@@ -304,5 +340,6 @@ class PipeFcg : public Method {
 
 Method* make_pipefcg(bool naive) { return new PipeFcg(naive, false); }
 Method* make_pipegcr_w() { return new PipeFcg(false, true); }
+Method* make_pipefcg_theta() { return new PipeFcg(false, false, true); }
 
 }  // namespace pfk

@@ -49,6 +49,7 @@ static Method* make_method(int method, double sigma = NAN) {
     case PFK_PIPEFCG: return make_pipefcg(false);
     case PFK_PIPEFCG_NAIVE: return make_pipefcg(true);
     case PFK_PIPEGCR_W: return make_pipegcr_w();
+    case PFK_PIPEFCG_THETA: return make_pipefcg_theta();
     case PFK_PIPEGCR: return make_pipegcr();
     case PFK_PIPEFGMRES: return make_pipefgmres(sigma);
     case PFK_FCG: return make_fcg();

@@ -56,6 +56,7 @@ class Method {
 
 Method* make_pipefcg(bool naive);
 Method* make_pipegcr_w();
+Method* make_pipefcg_theta();
 Method* make_pipegcr();
 Method* make_pipefgmres(double sigma);
 Method* make_fcg();

@@ -24,7 +24,7 @@ PFK_OK, PFK_PENDING = 0, 1
 STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "oom", -3: "cuda", -4: "breakdown",
                 -5: "not_converged", -6: "timeout", -7: "cancelled", -8: "busy"}
 METHODS = {"fcg": 0, "pipefcg": 1, "gcr": 2, "pipegcr": 3, "fgmres": 4, "pipefgmres": 5, "pipefcg_naive": 6,
-           "pipegcr_w": 7}
+           "pipegcr_w": 7, "pipefcg_theta": 8}
 PC_KINDS = {"none": 0, "jacobi": 1, "inner_pcg": 2, "chebyshev": 3, "noisy": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 OP_KINDS = {"stencil2d": 0, "stencil3d": 1, "csr": 2}

@@ -97,3 +97,25 @@ def test_noisy_pipefcg_trajectory_parity(ctx):
     pc = pfk.Preconditioner.noisy(ctx, op, 1e-3, bank)
     x, info, hist = pfk.solve(ctx, op, pc, t["b"], method="pipefcg", mmax=32, rtol=1e-10, maxit=200, history=400)
     check_solve(hist, info, ref, alts, rtol=1e-10)
+
+
+def test_theta_variant_toy_and_trajectory(ctx):
+    """eq. (proj) variant with the noisy B: converges like Alg. 8 (error <= 1e-2 eta
+    after 60 iterations) and follows the oracle's trajectory (envelope protocol)."""
+    from paper_1511_07226_gb300 import pfk
+    t = W.toy_diagonal()
+    xs = t["b"] / t["diag"]
+    bank = W.noise_bank(100, 500, seed_item=5)
+    op = _diag_operator(ctx, t["diag"])
+    pc = pfk.Preconditioner.noisy(ctx, op, 1e-3, bank)
+    x, info, _ = pfk.solve(ctx, op, pc, t["b"], method="pipefcg_theta", mmax=32, rtol=0.0, maxit=60,
+                           true_residual_check=False)
+    pc.close()
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-5
+    aop = O.DiagonalOperator(t["diag"])
+    prm = K.Params(mmax=32, rtol=1e-10, maxit=200)
+    ref, alts = oracle_with_envelope("pipefcg_theta", aop, lambda: PC.NoisyPC(1e-3, bank), t["b"], prm)
+    pc = pfk.Preconditioner.noisy(ctx, op, 1e-3, bank)
+    x, info, hist = pfk.solve(ctx, op, pc, t["b"], method="pipefcg_theta", mmax=32, rtol=1e-10, maxit=200,
+                              history=400)
+    check_solve(hist, info, ref, alts, rtol=1e-10)

@@ -43,7 +43,7 @@ def test_config1_csr_jacobi(ctx):
     assert e_gpu <= 10 * e_ora + 1e-12
 
 
-@pytest.mark.parametrize("method", ["pipefcg", "pipefcg_naive"])
+@pytest.mark.parametrize("method", ["pipefcg", "pipefcg_naive", "pipefcg_theta"])
 @pytest.mark.parametrize("mmax,trunc", [(30, "standard"), (5, "standard"), (4, "restart"), (1, "standard")])
 def test_3d_inner_pcg(ctx, method, mmax, trunc):
     from paper_1511_07226_gb300 import pfk
