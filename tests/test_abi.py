@@ -97,3 +97,13 @@ def test_struct_layouts_match_c_header(tmp_path):
         assert int(got[cname]) == C.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_storage_counts_match_the_paper_golden_file(lib):
+    """tests/golden/storage_counts.txt holds the paper's stated vector counts."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "storage_counts.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 7
+    for method, a, b, *_ in rows:
+        for nu in (1, 5, 30, 32):
+            assert pfk.storage_vectors(method, nu) == int(a) * nu + int(b), (method, nu)

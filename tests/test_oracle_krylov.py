@@ -296,16 +296,22 @@ def test_breakdown_restart_counting():
 @pytest.mark.parametrize("eta_noise", [1e-2, 1e-4])
 @pytest.mark.parametrize("seed", range(5))
 def test_toy_noise_experiment(eta_noise, seed):
-    """Fig. FCGtoy: n = 100, kappa = 5, b = 1/sqrt(n), nu_max = n, B(r) = r + eta ||r|| xi."""
-    t = W.toy_diagonal()
+    """Fig. FCGtoy: n = 100, kappa = 5, b = 1/sqrt(n), nu_max = n, B(r) = r + eta ||r|| xi
+    (parameters read from tests/golden/toy_experiment.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "toy_experiment.txt")
+    g = dict(ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#"))
+    t = W.toy_diagonal(n=int(g["n"]), kappa=float(g["condition_number"]))
+    assert np.allclose(t["b"], float(g["b_entry"]))
+    assert np.isclose(t["diag"].max() / t["diag"].min(), float(g["condition_number"]))
     A = O.DiagonalOperator(t["diag"])
     b = t["b"]
     xs = b / t["diag"]
     best = {}
     for m in ("fcg", "pipefcg", "pipefcg_naive"):
         B = PC.NoisyPC(eta_noise, W.noise_bank(100, 500, seed_item=seed))
-        r = K.solve(m, A, B, b, prm=K.Params(mmax=100, rtol=0.0, maxit=60, true_residual_check=False,
-                                            trace=True))
+        r = K.solve(m, A, B, b, prm=K.Params(mmax=int(g["nu_max"]), rtol=0.0, maxit=60,
+                                            true_residual_check=False, trace=True))
         errs = [np.linalg.norm(tr["x"] - xs) / np.linalg.norm(xs) for tr in r.trace]
         best[m] = (min(errs), errs[-1])
     assert best["fcg"][0] <= 1e-2 * eta_noise
