@@ -16,6 +16,10 @@ The flexible methods accept any, possibly nonlinear, map v -> B(v)
 * ``NoisyPC``         -- B(r) = r + eta ||r|| xi / ||xi|| with Gaussian xi,
                          the pathological preconditioner of Fig. FCGtoy.
 * ``DensePC``         -- B(v) = M v for a given matrix (e.g. A^-1).
+* ``BlockUpperPC``    -- the right preconditioner of the nested Stokes
+                         experiment (Sec. 6, ex43): B = [K_hat B^T; 0 S_hat]^-1
+                         with S_hat diagonal and K_hat^-1 an inexact inner
+                         flexible Krylov solve of the viscous block.
 
 Reduced-precision copies (``precision='fp32'`` / ``'bf16'``) emulate the
 mixed-precision preconditioners: the preconditioner's copy of A stores the
@@ -251,3 +255,41 @@ class Chebyshev:
             d = (dt(rho_new * rho) * d + dt(2.0 * rho_new / delta) * (self.dinv * r)).astype(dt)
             rho = rho_new
         return x.astype(np.float64)
+
+
+class BlockUpperPC:
+    """B(v) = [K_hat B^T; 0 S_hat]^-1 v for v = (v_u, v_p), the block
+    upper-triangular preconditioner of Sec. 6 (ex43):
+
+        y_p = S_hat^-1 v_p,  y_u = K_hat^-1 (v_u - B^T y_p),
+
+    S_hat a diagonal (``schur_diag``), K_hat^-1 an inner solve of K y_u = t
+    with ``inner_method`` from zero, Jacobi-preconditioned, ending at the
+    inner tolerance (natural norm), at ``inner_maxit`` iterations or at a norm
+    breakdown (no restarts, no true-residual check).  ``Bt`` acts on the full
+    vector (zero rows for the pressure block).  Nonlinear through the inner
+    solve: a flexible outer method is required.
+    """
+
+    linear = False
+
+    def __init__(self, K, Bt, schur_diag, nu: int, inner_method: str = "pipefcg", inner_mmax: int = 30,
+                 inner_rtol: float = 1e-3, inner_maxit: int = 100):
+        from . import krylov
+        self.K, self.Bt, self.nu = K, Bt, int(nu)
+        self.sinv = 1.0 / np.asarray(schur_diag, dtype=np.float64)
+        self.method = inner_method
+        self.prm = krylov.Params(mmax=inner_mmax, rtol=inner_rtol, maxit=inner_maxit, max_restarts=0,
+                                 true_residual_check=False)
+        self.inner_iterations = []
+
+    def __call__(self, v):
+        from . import krylov
+        v = np.asarray(v, dtype=np.float64)
+        y = np.zeros_like(v)
+        y[self.nu:] = self.sinv * v[self.nu:]
+        t = v[:self.nu] - self.Bt(y)[:self.nu]
+        r = krylov.solve(self.method, self.K, JacobiPC(self.K), t, prm=self.prm)
+        self.inner_iterations.append(r.iterations)
+        y[:self.nu] = r.x
+        return y
