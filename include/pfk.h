@@ -86,7 +86,8 @@ typedef enum {
   PFK_PC_JACOBI = 1,     /* B(v) = D^-1 v */
   PFK_PC_INNER_PCG = 2,  /* inner_iters iterations of Jacobi-PCG (Alg. 3, M^-1 = D^-1) from 0 */
   PFK_PC_CHEBYSHEV = 3,  /* inner_iters Chebyshev-Jacobi sweeps from 0 */
-  PFK_PC_NOISY = 4       /* B(r) = r + eta ||r|| xi_j / ||xi_j|| (pfk_create_noisy_preconditioner) */
+  PFK_PC_NOISY = 4,      /* B(r) = r + eta ||r|| xi_j / ||xi_j|| (pfk_create_noisy_preconditioner) */
+  PFK_PC_BLOCK_UPPER = 5 /* nested block upper-triangular (pfk_create_block_preconditioner) */
 } pfk_pc_kind;
 
 typedef enum {
@@ -200,6 +201,31 @@ pfk_status pfk_create_preconditioner(pfk_context* ctx, const pfk_operator* op, c
  * PFK_ERR_INVALID (eta < 0, count < 1, a zero bank row), PFK_ERR_OOM, PFK_ERR_CUDA. */
 pfk_status pfk_create_noisy_preconditioner(pfk_context* ctx, const pfk_operator* op, double eta, const double* bank,
                                            int count, int bank_on_device, pfk_pc** pc);
+/* Inner solve of a nested preconditioner: a CG- or CR-type method (PFK_FCG,
+ * PFK_PIPEFCG, PFK_PIPEFCG_THETA, PFK_GCR, PFK_PIPEGCR, PFK_PIPEGCR_W) with a
+ * Jacobi preconditioner, from a zero guess, stopping when its natural norm
+ * falls below rtol times the initial one, at maxit iterations, or at a norm
+ * breakdown (no restarts, no true-residual check). */
+typedef struct {
+  int32_t method;
+  int32_t mmax;     /* 1..PFK_MAX_MMAX, standard truncation */
+  double rtol;
+  int32_t maxit;    /* >= 1; each application records this many iterations */
+  int32_t pad;
+} pfk_inner_solve;
+
+/* The block upper-triangular preconditioner of the paper's Stokes experiment
+ * (Sec. 6, ex43): for v = (v_u, v_p) with nu = K's size and N = Bt's size,
+ *   y_p = S_hat^-1 v_p,   y_u = K_hat^-1 (v_u - B^T y_p),
+ * S_hat = diag(schur_diag) (host, N - nu entries, finite and non-zero; copied),
+ * K_hat^-1 one inner solve (`inner`) of K y_u = t.  Bt is an N x N operator
+ * holding B^T in its first nu rows (zero rows for the pressure block).  K and
+ * Bt must outlive the preconditioner.  Nonlinear through the inner solve: use
+ * it with a flexible outer method (e.g. PFK_FGMRES, PFK_PIPEFGMRES).  An
+ * application is a fixed sequence of device launches, so outer solves record it
+ * in their CUDA graphs.  Errors: PFK_ERR_INVALID, PFK_ERR_OOM, PFK_ERR_CUDA. */
+pfk_status pfk_create_block_preconditioner(pfk_context* ctx, const pfk_operator* K, const pfk_operator* Bt,
+                                           const double* schur_diag, const pfk_inner_solve* inner, pfk_pc** pc);
 pfk_status pfk_destroy_preconditioner(pfk_pc* pc);
 /* y = B(v); device pointers of length n, must not overlap. */
 pfk_status pfk_pc_apply(pfk_context* ctx, const pfk_pc* pc, const double* v, double* y);

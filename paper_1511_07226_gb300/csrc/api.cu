@@ -14,6 +14,8 @@ pfk_status create_csr(pfk_context* ctx, const pfk_operator_desc* desc, pfk_opera
 pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc* desc, pfk_pc* pc);
 pfk_status create_noisy_pc(pfk_context* ctx, const pfk_operator* op, double eta, const double* bank, int count,
                            int bank_on_device, pfk_pc* pc);
+pfk_status create_nested_pc(pfk_context* ctx, const pfk_operator* K, const pfk_operator* Bt,
+                            const double* schur_diag, const pfk_inner_solve* inner, pfk_pc* pc);
 pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, const pfk_solve_params* prm,
                      const double* b, double* x, pfk_solve_info* info);
 pfk_status solve_workspace_bytes(int method, int mmax, int64_t n, int64_t* bytes);
@@ -226,8 +228,30 @@ pfk_status pfk_create_noisy_preconditioner(pfk_context* ctx, const pfk_operator*
   return PFK_OK;
 }
 
+pfk_status pfk_create_block_preconditioner(pfk_context* ctx, const pfk_operator* K, const pfk_operator* Bt,
+                                           const double* schur_diag, const pfk_inner_solve* inner, pfk_pc** out) {
+  CHECK_ARG(ctx, ctx && K && Bt && schur_diag && inner && out, "NULL argument");
+  CHECK_ARG(ctx, Bt->n > K->n, "Bt must be N x N with N larger than K's size");
+  CHECK_ARG(ctx, inner->mmax >= 1 && inner->mmax <= PFK_MAX_MMAX, "inner mmax out of range");
+  CHECK_ARG(ctx, inner->maxit >= 1 && inner->rtol >= 0.0, "inner maxit must be >= 1 and rtol >= 0");
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  pfk_pc* pc = new (std::nothrow) pfk_pc();
+  if (!pc) return PFK_ERR_OOM;
+  pc->device = ctx->device;
+  pc->stream = ctx->stream;
+  pfk_status s = create_nested_pc(ctx, K, Bt, schur_diag, inner, pc);
+  if (s != PFK_OK) {
+    pfk_destroy_preconditioner(pc);
+    return s;
+  }
+  *out = pc;
+  return PFK_OK;
+}
+
 pfk_status pfk_destroy_preconditioner(pfk_pc* pc) {
   if (!pc) return PFK_OK;
+  if (pc->nested) destroy_nested(pc);
   // as for operators: never dereference the (possibly destroyed) context
   cudaSetDevice(pc->device);
   cudaStreamSynchronize(pc->stream);
@@ -303,7 +327,10 @@ pfk_status pfk_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
             "unknown truncation");
   CHECK_ARG(ctx, params->norm == PFK_NORM_NATURAL || params->norm == PFK_NORM_UNPRECONDITIONED, "unknown norm");
   CHECK_ARG(ctx, !params->history || params->history_capacity >= 0, "negative history capacity");
-  CHECK_ARG(ctx, !pc || pc->op == op, "preconditioner was built for another operator");
+  // a nested block preconditioner is built from the blocks (K, B^T), not from
+  // the outer operator: it must match the outer operator's size
+  CHECK_ARG(ctx, !pc || pc->op == op || (pc->kind == PFK_PC_BLOCK_UPPER && pc->op->n == op->n),
+            "preconditioner was built for another operator");
   if (!method_supported(params->method)) {
     set_error(ctx, "method not available");
     return PFK_ERR_INVALID;

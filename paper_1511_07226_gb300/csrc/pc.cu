@@ -401,6 +401,7 @@ static cudaError_t chebyshev(const pfk_pc* pc, StencilT<V, C> A, const double* v
 
 cudaError_t pc_apply(const pfk_pc* pc, const double* v, double* out, const double* add, const int* status,
                      cudaStream_t st) {
+  if (pc->kind == PFK_PC_BLOCK_UPPER) return nested_apply(pc, v, out, add, status, st);
   const pfk_operator* op = pc->op;
   const int64_t n = op->n;
   if (pc->kind == PFK_PC_NONE || pc->kind == PFK_PC_JACOBI) {

@@ -159,6 +159,7 @@ struct pfk_pc {
   double* bank = nullptr;
   double* bank_inv_norm = nullptr;
   int bank_count = 0;
+  void* nested = nullptr;       // block upper-triangular preconditioner state (nested.cu)
 };
 
 namespace pfk {
@@ -256,6 +257,11 @@ cudaError_t op_apply(const pfk_operator* op, const double* x, double* y, const d
 // out = add + B(v) (add may be null).  `status` as above.
 cudaError_t pc_apply(const pfk_pc* pc, const double* v, double* out, const double* add, const int* status,
                      cudaStream_t st);
+
+// Nested block preconditioner (nested.cu).
+cudaError_t nested_apply(const pfk_pc* pc, const double* v, double* out, const double* add, const int* status,
+                         cudaStream_t st);
+void destroy_nested(pfk_pc* pc);
 
 // Sum of squares / dot products into a device scalar (deterministic order).
 cudaError_t dot_into(pfk_context* ctx, const double* a, const double* b, int64_t n, double* out, cudaStream_t st);

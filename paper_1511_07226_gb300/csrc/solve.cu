@@ -59,6 +59,20 @@ static Method* make_method(int method, double sigma = NAN) {
   }
 }
 
+// Methods usable as the inner solve of a nested preconditioner (device-only
+// control: no restarts, no cycle ends).
+Method* make_inner_method(int method) {
+  switch (method) {
+    case PFK_FCG:
+    case PFK_PIPEFCG:
+    case PFK_PIPEFCG_THETA:
+    case PFK_GCR:
+    case PFK_PIPEGCR:
+    case PFK_PIPEGCR_W: return make_method(method);
+    default: return nullptr;
+  }
+}
+
 bool method_supported(int method) {
   std::unique_ptr<Method> m(make_method(method));
   return m != nullptr;

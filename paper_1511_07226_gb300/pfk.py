@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "oom", -3: "cuda", -4:
                 -5: "not_converged", -6: "timeout", -7: "cancelled", -8: "busy"}
 METHODS = {"fcg": 0, "pipefcg": 1, "gcr": 2, "pipegcr": 3, "fgmres": 4, "pipefgmres": 5, "pipefcg_naive": 6,
            "pipegcr_w": 7, "pipefcg_theta": 8}
-PC_KINDS = {"none": 0, "jacobi": 1, "inner_pcg": 2, "chebyshev": 3, "noisy": 4}
+PC_KINDS = {"none": 0, "jacobi": 1, "inner_pcg": 2, "chebyshev": 3, "noisy": 4, "block_upper": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 OP_KINDS = {"stencil2d": 0, "stencil3d": 1, "csr": 2}
 STORAGE = {"matrix_free": 0, "csr": 1}
@@ -50,6 +50,11 @@ class SolveParams(C.Structure):
                 ("rtol", C.c_double), ("atol", C.c_double), ("maxit", C.c_int32), ("max_restarts", C.c_int32),
                 ("sigma", C.c_double), ("true_residual_check", C.c_int32), ("graph_iters", C.c_int32),
                 ("history", C.c_void_p), ("history_capacity", C.c_int32), ("profile", C.c_int32)]
+
+
+class InnerSolve(C.Structure):
+    _fields_ = [("method", C.c_int32), ("mmax", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class ServerParams(C.Structure):
@@ -90,6 +95,8 @@ _SIGS = {
     "pfk_destroy_preconditioner": (C.c_int, [C.c_void_p]),
     "pfk_create_noisy_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int, C.c_int,
                                                   C.POINTER(C.c_void_p)]),
+    "pfk_create_block_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                  C.POINTER(InnerSolve), C.POINTER(C.c_void_p)]),
     "pfk_pc_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pfk_default_params": (C.c_int, [C.POINTER(SolveParams)]),
     "pfk_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p,
@@ -281,6 +288,23 @@ class Preconditioner:
                                                       int(bk.shape[0]), 0, C.byref(h)), ctx.h)
         self.h = h
         self.kind, self.precision = "noisy", "fp64"
+        return self
+
+    @classmethod
+    def block_upper(cls, ctx: Context, K: Operator, Bt: Operator, schur_diag, inner_method: str = "pipefcg",
+                    inner_mmax: int = 30, inner_rtol: float = 1e-3, inner_maxit: int = 100):
+        """[K_hat B^T; 0 S_hat]^-1 with K_hat^-1 an inner solve (the Stokes nesting of Sec. 6)."""
+        sd = np.ascontiguousarray(schur_diag, dtype=np.float64)
+        inner = InnerSolve()
+        inner.method, inner.mmax = METHODS[inner_method], int(inner_mmax)
+        inner.rtol, inner.maxit = float(inner_rtol), int(inner_maxit)
+        self = cls.__new__(cls)
+        self.ctx, self.op, self.keep = ctx, Bt, (K, Bt)
+        h = C.c_void_p()
+        _check(load().pfk_create_block_preconditioner(ctx.h, K.h, Bt.h, C.c_void_p(sd.ctypes.data), C.byref(inner),
+                                                      C.byref(h)), ctx.h)
+        self.h = h
+        self.kind, self.precision = "block_upper", "fp64"
         return self
 
     def apply(self, v):

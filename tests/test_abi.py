@@ -107,3 +107,16 @@ def test_storage_counts_match_the_paper_golden_file(lib):
     for method, a, b, *_ in rows:
         for nu in (1, 5, 30, 32):
             assert pfk.storage_vectors(method, nu) == int(a) * nu + int(b), (method, nu)
+
+
+def test_inner_solve_struct_layout(tmp_path):
+    src = tmp_path / "inner.c"
+    src.write_text(f'#include <stdio.h>\n#include <stddef.h>\n#include "{pfk.HEADER}"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(pfk_inner_solve), '
+                   'offsetof(pfk_inner_solve, rtol), offsetof(pfk_inner_solve, maxit), '
+                   'offsetof(pfk_inner_solve, pad)); return 0; }')
+    exe = tmp_path / "inner"
+    subprocess.run(["gcc", "-std=c11", str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [C.sizeof(pfk.InnerSolve), pfk.InnerSolve.rtol.offset, pfk.InnerSolve.maxit.offset,
+                   pfk.InnerSolve.pad.offset]
