@@ -232,9 +232,9 @@ def main():
     ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase"],
                     help="--ncu-case problem: Gaussian-field Poisson (4 inner PCG) or two-phase advection "
                          "(8 Chebyshev sweeps)")
-    ap.add_argument("--extras", default="fcg,pipegcr,nu_sweep,batched,fgmres256,serve",
-                    help="comma-separated secondary measurements (fcg, pipegcr, nu_sweep, batched, fgmres256, "
-                         "serve) or 'none'")
+    ap.add_argument("--extras", default="fcg,pipegcr,nu_sweep,stokes,batched,fgmres256,serve",
+                    help="comma-separated secondary measurements (fcg, pipegcr, nu_sweep, stokes, batched, "
+                         "fgmres256, serve) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
@@ -472,6 +472,39 @@ def extra_nu_sweep(ctx, dev, args) -> dict:
                         f"at most {NU_SWEEP_MAXIT} iterations", "runs": out}
 
 
+def extra_stokes(ctx, dev, args) -> dict:
+    """The nesting of Sec. 6 (ex43 structure) on the Stokes-like sinker system:
+    outer FGMRES(30), unpreconditioned residual reduced by 1e6, right block
+    upper-triangular preconditioner whose velocity block is an inner solve
+    (Jacobi, natural-norm rtol 1e-3, at most 500 iterations: point Jacobi
+    needs more inner iterations than the paper's block-Jacobi/CG subdomain
+    solves) by each inner method -- the comparison of the paper's Table ex43."""
+    import torch
+    from paper_1511_07226_gb300 import pfk
+    from workloads import stokes as S
+    d = S.stokes2d(n=STOKES_N)
+    A = pfk.Operator.csr(ctx, *d["A"])
+    Kop = pfk.Operator.csr(ctx, *d["K"])
+    Bt = pfk.Operator.csr(ctx, *d["Bt"])
+    b = torch.from_numpy(d["b"]).to(dev)
+    runs = []
+    for inner in ("fcg", "pipefcg", "gcr", "pipegcr"):
+        pc = pfk.Preconditioner.block_upper(ctx, Kop, Bt, d["schur_diag"], inner, 30, STOKES_INNER_RTOL,
+                                            STOKES_INNER_MAXIT)
+        x = torch.zeros_like(b)
+        _, info, _ = pfk.solve(ctx, A, pc, b, x0=x, method="fgmres", mmax=30, rtol=1e-6, maxit=200,
+                               graph_iters=1)
+        runs.append({"inner": inner, "outer_iterations": info["iterations"], "status": info["status_name"],
+                     "time_ms": info["time_ms"],
+                     "ms_per_outer_iteration": info["time_ms"] / max(info["iterations"], 1),
+                     "true_rel_residual": info["rnorm_true"] / info["bnorm"]})
+        pc.close()
+    return {"workload": f"2D MAC Stokes-like sinker (contrast 25), n = {STOKES_N} ({d['N']} unknowns), outer "
+                        f"FGMRES(30) to 1e-6, block upper-triangular B with inner solve rtol {STOKES_INNER_RTOL} / "
+                        f"{STOKES_INNER_MAXIT} its",
+            "runs": runs}
+
+
 def extra_batched(ctx, dev, args) -> dict:
     """512 independent 2D systems (sides 32..256) in one persistent PIPEFCG launch."""
     import workloads as W
@@ -577,8 +610,11 @@ MAX_RESTARTS = 200
 FGMRES256_ITERS = 900
 BATCHED_MAXIT = 4000
 NU_SWEEP_MAXIT = 4000
+STOKES_N = 256
+STOKES_INNER_RTOL = 1e-3
+STOKES_INNER_MAXIT = 500
 
-EXTRAS = {"fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
+EXTRAS = {"fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "stokes": extra_stokes, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
 
 
 # Iterations of one 128^3 solve for the reference arm's extrapolation: the
