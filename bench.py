@@ -234,7 +234,7 @@ def main():
                          "(8 Chebyshev sweeps)")
     ap.add_argument("--extras", default="fcg,pipegcr,nu_sweep,stokes,batched,fgmres256,serve",
                     help="comma-separated secondary measurements (fcg, pipegcr, nu_sweep, stokes, batched, "
-                         "fgmres256, serve) or 'none'")
+                         "fgmres256, serve; serve_sweep is opt-in) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
@@ -560,47 +560,66 @@ def extra_fgmres256(ctx, dev, args) -> dict:
     return out
 
 
-def extra_serve(ctx, dev, args) -> dict:
-    """A bounded prefix of the Poisson-arrival request stream (mean 200 req/s,
-    3D sides U[32,160], contrast 1e2..1e6, method drawn from PIPEFCG / PIPEGCR /
-    PIPEFGMRES) replayed in real time through the continuous-batching server."""
+def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0) -> dict:
+    """Replays requests through a fresh server at their arrival times scaled by
+    rate_scale (2 = twice as far apart); returns latency and throughput."""
     import workloads as W
     from paper_1511_07226_gb300 import pfk
     meth = {0: "pipefcg", 1: "pipegcr", 2: "pipefgmres"}
-    reqs = W.request_stream(count=args.serve_requests)
-    probs = [W.request_problem(r) for r in reqs]
-    srv = pfk.Server(ctx, workers=args.serve_workers)
+    srv = pfk.Server(ctx, workers=workers)
     kw = dict(mmax=30, rtol=1e-8, maxit=20000, max_restarts=MAX_RESTARTS)
     # warm-up: one small request per method (graphs, module loading)
     for m in meth.values():
         p = W.poisson3d_gaussian(n=24, ell=4.0, log_contrast=1.0, config_id=5, item_id=999_999)
         srv.poll(srv.submit(p["dims"], p["eta"], p["b"], method=m, **kw))
-    results = [None] * len(reqs)
-
-    def collect(tickets):
-        for j, t in tickets:
-            results[j] = srv.poll(t)
-
     tickets = []
     t0 = time.perf_counter()
     for j, (r, p) in enumerate(zip(reqs, probs)):
-        delay = r["t"] - reqs[0]["t"] - (time.perf_counter() - t0)
+        delay = rate_scale * (r["t"] - reqs[0]["t"]) - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
         tickets.append((j, srv.submit(p["dims"], p["eta"], p["b"], method=meth[r["method"]], **kw)))
-    collect(tickets)
+    results = [srv.poll(t) for _, t in tickets]
     wall = time.perf_counter() - t0
     srv.close()
     lat = np.array([res[2] for res in results])
-    ok = sum(res[1]["status_name"] == "ok" for res in results)
     unknowns = int(sum(r["side"] ** 3 for r in reqs))
-    return {"workload": f"first {len(reqs)} requests of the seeded stream, replayed at their arrival times",
-            "workers": args.serve_workers, "requests": len(reqs), "converged": int(ok),
-            "offered_rate_per_s": len(reqs) / max(reqs[-1]["t"] - reqs[0]["t"], 1e-9),
+    return {"workers": workers, "requests": len(reqs),
+            "converged": int(sum(res[1]["status_name"] == "ok" for res in results)),
+            "offered_rate_per_s": len(reqs) / max(rate_scale * (reqs[-1]["t"] - reqs[0]["t"]), 1e-9),
             "solves_per_s": len(reqs) / wall, "unknowns_per_s": unknowns / wall,
             "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
             "max_latency_ms": float(lat.max()),
             "max_true_rel_residual": float(max(res[1]["rnorm_true"] / res[1]["bnorm"] for res in results))}
+
+
+def extra_serve(ctx, dev, args) -> dict:
+    """A bounded prefix of the Poisson-arrival request stream (mean 200 req/s,
+    3D sides U[32,160], contrast 1e2..1e6, method drawn from PIPEFCG / PIPEGCR /
+    PIPEFGMRES) replayed in real time through the continuous-batching server."""
+    import workloads as W
+    reqs = W.request_stream(count=args.serve_requests)
+    probs = [W.request_problem(r) for r in reqs]
+    out = _serve_replay(ctx, reqs, probs, args.serve_workers)
+    out["workload"] = f"first {len(reqs)} requests of the seeded stream, replayed at their arrival times"
+    return out
+
+
+def extra_serve_sweep(ctx, dev, args) -> dict:
+    """Offered-load sweep of the serving loop (not in the default run): the
+    first 16 requests of the stream replayed at 1, 4 and 200 (as generated)
+    requests/s with 8 workers, and at 200 req/s with 1 worker (no overlap of
+    solves) for the concurrency gain."""
+    import workloads as W
+    reqs = W.request_stream(count=16)
+    probs = [W.request_problem(r) for r in reqs]
+    span = reqs[-1]["t"] - reqs[0]["t"]
+    runs = []
+    for rate in (1.0, 4.0, None):
+        scale = 1.0 if rate is None else (len(reqs) / rate) / span
+        runs.append(_serve_replay(ctx, reqs, probs, 8, scale))
+    runs.append(_serve_replay(ctx, reqs, probs, 1, 1.0))
+    return {"workload": "first 16 requests of the seeded stream at several offered rates", "runs": runs}
 
 
 # Residual-replacement restarts allowed in the batched and serving legs: with
@@ -614,7 +633,8 @@ STOKES_N = 256
 STOKES_INNER_RTOL = 1e-3
 STOKES_INNER_MAXIT = 500
 
-EXTRAS = {"fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "stokes": extra_stokes, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
+EXTRAS = {"fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "stokes": extra_stokes,
+          "serve_sweep": extra_serve_sweep, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
 
 
 # Iterations of one 128^3 solve for the reference arm's extrapolation: the
