@@ -56,6 +56,21 @@ NCU_TRAFFIC = {"source_sha256": "f132cf64f45e1ba8b2e6effa03ac6c24bbc14f75b39213e
                "captured_on": "96^3, scaled by 128^3/96^3"}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, ms_max: float) -> float:
+    """Whole-job solves/s of `world` replicas, each taking at most ms_max per solve."""
+    return world * 1e3 / ms_max
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -307,11 +322,8 @@ def main():
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * 1e3 / ms_max
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = replica_value(world, ms_max)
 
     its = int(np.median([i["iterations"] for i in infos]))
     launches = int(sum(i["kernel_launches"] for i in infos))
