@@ -244,15 +244,28 @@ def main():
     ap.add_argument("--maxit", type=int, default=10000)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--method", default="pipefcg", help="method of the --ncu-case solve")
-    ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase"],
-                    help="--ncu-case problem: Gaussian-field Poisson (4 inner PCG) or two-phase advection "
-                         "(8 Chebyshev sweeps)")
+    ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase", "batched"],
+                    help="--ncu-case problem: Gaussian-field Poisson (4 inner PCG), two-phase advection "
+                         "(8 Chebyshev sweeps), or the first --n systems of the batched workload")
     ap.add_argument("--extras", default="fcg,pipegcr,nu_sweep,stokes,batched,fgmres256,serve",
                     help="comma-separated secondary measurements (fcg, pipegcr, nu_sweep, stokes, batched, "
                          "fgmres256, serve; serve_sweep is opt-in) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
+    if args.ncu_case and args.case == "batched":
+        import workloads as W
+        from paper_1511_07226_gb300 import pfk
+        ctx = pfk.Context(0)
+        sides = W.batched2d_sides()[: args.n]
+        sys_ = [W.batched2d_system(j, int(sd)) for j, sd in enumerate(sides)]
+        ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys_]
+        _, infos, _ = pfk.solve_batched(ctx, ops, [c["b"] for c in sys_], pc_kind="inner_pcg", inner_iters=4,
+                                        precision="fp32", mmax=20, rtol=1e-8, maxit=args.maxit,
+                                        block_threads=256)
+        print(json.dumps({"ncu_case": "batched", "systems": len(ops),
+                          "iterations": int(sum(i["iterations"] for i in infos))}))
+        return
     if args.ncu_case:
         from paper_1511_07226_gb300 import pfk
         ctx = pfk.Context(0)

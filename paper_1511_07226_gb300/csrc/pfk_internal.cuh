@@ -233,7 +233,7 @@ __device__ __forceinline__ bool combine_block_partials(const double* smem, int n
 template <int ND>
 __device__ __forceinline__ bool reduce_last_block(const double (&acc)[ND], int nd, double* partials, int stride,
                                                   unsigned int* counter, double* smem, double* sums) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     if (j < nd) {
