@@ -20,8 +20,10 @@
 // threads and blocks in FP64.
 #include "pfk_internal.cuh"
 #include "stencil.cuh"
+#include "stencil_tma.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 namespace pfk {
 
@@ -316,6 +318,99 @@ __global__ void __launch_bounds__(kThreads) cheb_last_kernel(int64_t n, const V*
 // Host side
 // ---------------------------------------------------------------------------
 
+PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }();
+  return fn;
+}
+
+bool tma_make_map(CUtensorMap* map, const void* base, CUtensorMapDataType type, int es, int nx, int ny, int nz,
+                  int box_w, int box_h) {
+  auto fn = tma_encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return fn(map, type, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Maps of the operator's coefficient arrays and the walked input m (and, for
+// the Chebyshev sweep, dinv, r, x).  False if any map cannot be made.
+template <typename C>
+static bool tma_maps(TmaMaps& M, const pfk_operator* op, const float* m, const C* d, const C* kx, const C* ky,
+                     const C* kz, const C* dinv, const float* r, const float* x) {
+  const int nx = op->nx, ny = op->ny, nz = op->nz, es = (int)sizeof(C);
+  const CUtensorMapDataType ct = sizeof(C) == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  bool ok = tma_make_map(&M.m, m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nx, ny, nz, kTmaMW, kTmaMH) &&
+            tma_make_map(&M.kx, kx, ct, es, nx, ny, nz, kTmaMW, kTileY) &&
+            tma_make_map(&M.ky, ky, ct, es, nx, ny, nz, kTileX, kTmaKyH) &&
+            tma_make_map(&M.d, d, ct, es, nx, ny, nz, kTileX, kTileY) &&
+            tma_make_map(&M.kz, kz, ct, es, nx, ny, nz, kTileX, kTileY);
+  if (ok && dinv)
+    ok = tma_make_map(&M.dinv, dinv, ct, es, nx, ny, nz, kTileX, kTileY) &&
+         tma_make_map(&M.r, r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nx, ny, nz, kTileX, kTileY) &&
+         tma_make_map(&M.x, x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nx, ny, nz, kTileX, kTileY);
+  return ok;
+}
+
+// Resident blocks of a TMA walk kernel (its dynamic shared memory included).
+template <typename K>
+static int tma_slots(K kernel, int smem, int num_sms) {
+  static const int per_sm = [&]() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kTileThreads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      b = 1;
+    }
+    return b < 1 ? 1 : b;
+  }();
+  return per_sm * num_sms;
+}
+
+// Work decomposition (32 x 8 tiles, z-chunks sized to the resident blocks) and
+// the operator's advection weights.
+static TmaWalkArgs tma_args(const pfk_operator* op, int slots, const int* status, int* err) {
+  TmaWalkArgs a{};
+  a.nx = op->nx; a.ny = op->ny; a.nz = op->nz;
+  a.tiles_x = (op->nx + kTileX - 1) / kTileX;
+  a.tiles_y = (op->ny + kTileY - 1) / kTileY;
+  a.zc = tiled_stencil_zc(a.tiles_x * a.tiles_y, op->nz, slots);
+  a.zchunks = (op->nz + a.zc - 1) / a.zc;
+  a.a0 = (float)op->adv[0]; a.a1 = (float)op->adv[1]; a.a2 = (float)op->adv[2];
+  a.up0 = op->upw[0] < 0 ? -1 : 1; a.up1 = op->upw[1] < 0 ? -1 : 1; a.up2 = op->upw[2] < 0 ? -1 : 1;
+  a.status = status;
+  a.err = err;
+  return a;
+}
+
+template <typename C, bool CHEB>
+static cudaError_t tma_launch(const TmaMaps& M, TmaWalkArgs a, const pfk_operator* op, cudaStream_t st) {
+  using L = TmaStage<float, C, CHEB ? 3 : 0>;
+  const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
+  const int slots = adv ? tma_slots(tma_walk_kernel<C, true, CHEB>, L::smem, op->ctx->num_sms)
+                        : tma_slots(tma_walk_kernel<C, false, CHEB>, L::smem, op->ctx->num_sms);
+  const TmaWalkArgs d = tma_args(op, slots, a.status, a.err);
+  a.tiles_x = d.tiles_x; a.tiles_y = d.tiles_y; a.zc = d.zc; a.zchunks = d.zchunks;
+  a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
+  a.a0 = d.a0; a.a1 = d.a1; a.a2 = d.a2; a.up0 = d.up0; a.up1 = d.up1; a.up2 = d.up2;
+  const int units = a.tiles_x * a.tiles_y * a.zchunks;
+  if (adv) tma_walk_kernel<C, true, CHEB><<<units, kTileThreads, L::smem, st>>>(M, a);
+  else tma_walk_kernel<C, false, CHEB><<<units, kTileThreads, L::smem, st>>>(M, a);
+  return cudaGetLastError();
+}
+
 template <typename V, typename C>
 static StencilT<V, C> make_stencil(const pfk_operator* op, const C* d, const C* kx, const C* ky, const C* kz,
                                    const C* dinv) {
@@ -350,7 +445,28 @@ static cudaError_t inner_pcg(const pfk_pc* pc, StencilT<V, C> A, const double* v
   PcCtl* ctl = pc->ctl;
   pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, 0, k, pc->partials, status);
   pcg_b_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, r, nullptr, p[0], x, ctl, 0, status);
+  // reduced precision on an aligned 3-D grid: the TMA-pipelined walk
+  bool tma = false;
+  TmaMaps maps[2];
+  if constexpr (std::is_same<V, float>::value) {
+    tma = tma_walk_usable(op->nx, op->nz, {p[0], p[1], s, A.d, A.kx, A.ky, A.kz}) &&
+          tma_maps<C>(maps[0], op, p[0], A.d, A.kx, A.ky, A.kz, nullptr, nullptr, nullptr) &&
+          tma_maps<C>(maps[1], op, p[1], A.d, A.kx, A.ky, A.kz, nullptr, nullptr, nullptr);
+  }
   auto pcg_c = [&](const V* pv, int i) {
+    if constexpr (std::is_same<V, float>::value) {
+      if (tma) {
+        TmaWalkArgs a{};
+        a.s = s;
+        a.ctl = ctl;
+        a.i = i;
+        a.partials = pc->partials;
+        a.status = status;
+        a.err = (int*)pc->ctx->scratch_counter + 3;
+        tma_launch<C, false>(maps[pv == p[0] ? 0 : 1], a, op, st);
+        return;
+      }
+    }
     if (T.adv) pcg_c_kernel<V, C, true><<<tblocks, kTileThreads, 0, st>>>(T, pv, s, ctl, i, pc->partials, status);
     else pcg_c_kernel<V, C, false><<<tblocks, kTileThreads, 0, st>>>(T, pv, s, ctl, i, pc->partials, status);
   };
@@ -383,10 +499,34 @@ static cudaError_t chebyshev(const pfk_pc* pc, StencilT<V, C> A, const double* v
   const int slots = adv ? tiled_stencil_slots(cheb_sweep_kernel<V, C, true>, pc->ctx->num_sms)
                         : tiled_stencil_slots(cheb_sweep_kernel<V, C, false>, pc->ctx->num_sms);
   const int units = tiled_stencil_setup<V, C>(T, op, A.d, A.kx, A.ky, A.kz, slots);
+  // reduced precision on an aligned 3-D grid: the TMA-pipelined walk
+  bool tma = false;
+  TmaMaps maps[2];
+  if constexpr (std::is_same<V, float>::value) {
+    tma = tma_walk_usable(op->nx, op->nz, {dv[0], dv[1], r, x, A.d, A.kx, A.ky, A.kz, A.dinv}) &&
+          tma_maps<C>(maps[0], op, dv[0], A.d, A.kx, A.ky, A.kz, A.dinv, r, x) &&
+          tma_maps<C>(maps[1], op, dv[1], A.d, A.kx, A.ky, A.kz, A.dinv, r, x);
+  }
   cheb_init_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, v, r, dv[0], (V)(1.0 / theta), status);
   for (int j = 0; j + 1 < k; ++j) {
     const double rho_new = 1.0 / (2.0 * sigma1 - rho);
     const V c1 = (V)(rho_new * rho), c2 = (V)(2.0 * rho_new / delta);
+    if constexpr (std::is_same<V, float>::value) {
+      if (tma) {
+        TmaWalkArgs a{};
+        a.dn = dv[(j + 1) & 1];
+        a.r = r;
+        a.x = x;
+        a.first = j == 0;
+        a.c1 = c1;
+        a.c2 = c2;
+        a.status = status;
+        a.err = (int*)pc->ctx->scratch_counter + 3;
+        tma_launch<C, true>(maps[j & 1], a, op, st);
+        rho = rho_new;
+        continue;
+      }
+    }
     if (T.adv)
       cheb_sweep_kernel<V, C, true><<<units, kTileThreads, 0, st>>>(T, A.dinv, dv[j & 1], dv[(j + 1) & 1], r, x, j,
                                                                     c1, c2, status);
