@@ -97,10 +97,24 @@ struct OpView {
   const double* vals;
 };
 
+// ADV = false (no advection): the upwind additions are zero and are not
+// evaluated (an FP64 add per neighbour saved).
+template <bool ADV>
 __device__ __forceinline__ double op_row_stencil(const OpView& A, const double* __restrict__ m, int64_t c, int i,
                                                  int j, int k) {
   const int64_t sxy = (int64_t)A.nx * A.ny;
   double acc = A.d[c] * m[c];
+  if (!ADV) {
+    if (i > 0) acc = fma(-A.kx[c - 1], m[c - 1], acc);
+    if (i < A.nx - 1) acc = fma(-A.kx[c], m[c + 1], acc);
+    if (j > 0) acc = fma(-A.ky[c - A.nx], m[c - A.nx], acc);
+    if (j < A.ny - 1) acc = fma(-A.ky[c], m[c + A.nx], acc);
+    if (A.ndim == 3) {
+      if (k > 0) acc = fma(-A.kz[c - sxy], m[c - sxy], acc);
+      if (k < A.nz - 1) acc = fma(-A.kz[c], m[c + sxy], acc);
+    }
+    return acc;
+  }
   if (i > 0) acc = fma(-(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)), m[c - 1], acc);
   if (i < A.nx - 1) acc = fma(-(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)), m[c + 1], acc);
   if (j > 0) acc = fma(-(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)), m[c - A.nx], acc);
@@ -123,7 +137,7 @@ __device__ __forceinline__ double op_row_csr(const OpView& A, const double* __re
 // w values and stored s_k values are staged in shared memory and lane jj of
 // the warp sums w_e s_{k_jj,e} over the chunk (the same transposed window dot
 // as in the PIPEFCG pass).
-template <int NW, bool STENCIL>
+template <int NW, bool STENCIL, bool ADV = false>
 __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_dots(GcrArgs a, OpView A) {
   SolveCtl* ctl = a.ctl;
   if (ctl->status != kRun) return;
@@ -166,7 +180,7 @@ __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_do
           valid = true;
           c = row * A.nx + ix;
           const int irow = (int)row;
-          wv = op_row_stencil(A, a.u, c, ix, irow % A.ny, irow / A.ny);
+          wv = op_row_stencil<ADV>(A, a.u, c, ix, irow % A.ny, irow / A.ny);
         }
       } else {
         c = ch * 32 + lane;
@@ -178,14 +192,23 @@ __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_do
     }
     if (valid) {
       const double rv = a.r[c];
+      // the window's s_k values, eight loads in flight at a time, parked in
+      // shared memory for the transposed dots
+#pragma unroll
+      for (int j0 = 0; j0 < NW; j0 += 8) {
+        double sv[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          sv[jj] = (j0 + jj < nu) ? __ldg(&a.S[s_off[j0 + jj] + c]) : 0.0;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (j0 + jj < nu) my_sk[(j0 + jj) * kGcrStride] = sv[jj];
+      }
       a.w[c] = wv;
       a.t[c] = wv - rv;
       g0 = fma(rv, wv, g0);
       g1 = fma(wv, wv, g1);
       g2 = fma(rv, rv, g2);
-#pragma unroll
-      for (int j = 0; j < NW; ++j)
-        if (j < nu) my_sk[j * kGcrStride] = a.S[s_off[j] + c];
     } else {
 #pragma unroll
       for (int j = 0; j < NW; ++j)
@@ -286,6 +309,7 @@ class PipeGcr : public Method {
     A.u0 = op->upw[0]; A.u1 = op->upw[1]; A.u2 = op->upw[2];
     A.rowptr = op->rowptr; A.colidx = op->colidx; A.vals = op->vals;
     const bool stencil = op->rowptr == nullptr;
+    const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
     const int tmpl = gcr_template(mmax_);
     const int ablocks = stream_blocks(env.ctx, N_, 4);
     const int64_t chunks = stencil ? (int64_t)((op->nx + 31) / 32) * op->ny * op->nz : (N_ + 31) / 32;
@@ -298,17 +322,20 @@ class PipeGcr : public Method {
     switch (tmpl) {
       case 8:
         pipegcr_advance<8><<<ablocks, kThreads, 0, env.st>>>(a);
-        if (stencil) pipegcr_apply_dots<8, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        if (stencil && adv) pipegcr_apply_dots<8, true, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        else if (stencil) pipegcr_apply_dots<8, true, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         else pipegcr_apply_dots<8, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         break;
       case 16:
         pipegcr_advance<16><<<ablocks, kThreads, 0, env.st>>>(a);
-        if (stencil) pipegcr_apply_dots<16, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        if (stencil && adv) pipegcr_apply_dots<16, true, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        else if (stencil) pipegcr_apply_dots<16, true, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         else pipegcr_apply_dots<16, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         break;
       default:
         pipegcr_advance<32><<<ablocks, kThreads, 0, env.st>>>(a);
-        if (stencil) pipegcr_apply_dots<32, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        if (stencil && adv) pipegcr_apply_dots<32, true, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        else if (stencil) pipegcr_apply_dots<32, true, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         else pipegcr_apply_dots<32, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         break;
     }
