@@ -233,8 +233,13 @@ pfk_status pfk_submit(pfk_server* srv, const pfk_request* req, uint64_t* ticket)
     it->eta.assign(req->op.eta, req->op.eta + n);
     it->desc.eta = it->eta.data();
   } else if (req->op.kind == PFK_CSR) {
-    if (req->op.csr_on_device || !req->op.rowptr || req->op.n <= 0) {
-      set_error(nullptr, "requests need host CSR arrays");
+    if (req->op.csr_on_device || !req->op.rowptr || req->op.n <= 0 || req->op.nnz < 0 ||
+        (req->op.nnz > 0 && (!req->op.colidx || !req->op.vals))) {
+      set_error(nullptr, "requests need host CSR arrays (row pointers, columns, values)");
+      return PFK_ERR_INVALID;
+    }
+    if (req->op.rowptr[0] != 0 || req->op.rowptr[req->op.n] != req->op.nnz) {
+      set_error(nullptr, "CSR row pointers must run from 0 to nnz");
       return PFK_ERR_INVALID;
     }
     n = req->op.n;
