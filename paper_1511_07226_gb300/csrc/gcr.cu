@@ -8,17 +8,21 @@
 //       q_{i-1} = m_{i-1} + ...
 //     into ring slot (i-1) mod (mmax+1), then x_i, r_i and u_i (tilde-u) with
 //     alpha_{i-1};
-//  2. pipegcr_apply_dots<NW>: w_i = A u_i (stencil or CSR) fused with the
-//     single reduction of the iteration: gamma_i = <r_i, w_i>, delta_i =
-//     <w_i, w_i>, ||r_i||^2 and <w_i, s_k> for the nu_i stored s_k; writes the
-//     preconditioner input t = w_i - r_i; the last block computes beta, eta_i,
-//     alpha_i and the status;
+//  2. the iteration's single reduction with w_i = A u_i: gamma_i = <r_i, w_i>,
+//     delta_i = <w_i, w_i>, ||r_i||^2 and <w_i, s_k> for the nu_i stored s_k,
+//     and the preconditioner input t = w_i - r_i; the last block computes beta,
+//     eta_i, alpha_i and the status.  For a stencil operator this is two
+//     kernels -- the tiled z-marching walk (w, t and the three scalar dots,
+//     handed over in the control block) and a streaming pass over w and the
+//     window (pipegcr_window_dots) -- because the fused one-kernel form,
+//     pipegcr_apply_dots (kept for CSR operators), is latency-bound;
 //  3. the preconditioner, m_i = u_i + B(w_i - r_i).
 //
 // Unlike Alg. 8 the operator product w_i = A u_i is explicit, so the
 // reduction overlaps only the preconditioner (Sec. 4.2).
 #include "pfk_internal.cuh"
 #include "solver.cuh"
+#include "stencil.cuh"
 
 namespace pfk {
 
@@ -248,6 +252,96 @@ __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_do
   cgcr_iteration_scalars(ctl, i, nu, s_sum[0], s_sum[1], s_sum[2], s_sum + 3);
 }
 
+// ---- stencil operators: w = A u by the tiled walk, then the window dots ----
+
+// Epilogue of the walk: w = A u, t = w - r, and per-thread <r, w>, <w, w>, <r, r>.
+struct GcrApplyEpi {
+  double* __restrict__ w;
+  double* __restrict__ t;
+  const double* __restrict__ r;
+  double g0, g1, g2;
+  struct Pre {
+    double r;
+  };
+  __device__ __forceinline__ Pre pre(int64_t c) const { return Pre{r[c]}; }
+  __device__ __forceinline__ void operator()(int64_t c, double wv, double, const Pre& p) {
+    w[c] = wv;
+    t[c] = wv - p.r;
+    g0 = fma(p.r, wv, g0);
+    g1 = fma(wv, wv, g1);
+    g2 = fma(p.r, p.r, g2);
+  }
+};
+
+template <bool ADV>
+__global__ void __launch_bounds__(kTileThreads) pipegcr_apply_walk(TiledStencil<double, double> T, GcrArgs a) {
+  SolveCtl* ctl = a.ctl;
+  if (ctl->status != kRun) return;
+  GcrApplyEpi e{a.w, a.t, a.r, 0.0, 0.0, 0.0};
+  tiled_stencil_walk<double, double, ADV, 1>(T, a.u, e);
+  double acc[3] = {e.g0, e.g1, e.g2};
+  __shared__ double smem[(kTileThreads / 32) * 3];
+  __shared__ double sums[3];
+  if (reduce_last_block<3>(acc, 3, a.partials, 3, &ctl->counter, smem, sums) && threadIdx.x == 0) {
+    ctl->pend[0] = sums[0];
+    ctl->pend[1] = sums[1];
+    ctl->pend[2] = sums[2];
+  }
+}
+
+// <w_i, s_k> over the window, one register accumulator per window slot and
+// thread (independent FMAs, no shared-memory staging); the last block adds the
+// walk's gamma, delta, ||r||^2 and runs the scalar phase of iteration i.
+constexpr int kWinBlocksPerSm = 5;   // 93 registers at NW = 32
+
+template <int NW>
+__global__ void __launch_bounds__(kGcrThreads, kWinBlocksPerSm) pipegcr_window_dots(GcrArgs a, int stencil_flops) {
+  SolveCtl* ctl = a.ctl;
+  if (ctl->status != kRun) return;
+  constexpr int NWARPS = kGcrThreads / 32;
+  __shared__ size_t s_off[NW];
+  __shared__ double s_red[NWARPS * NW];
+  __shared__ double s_sum[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = ctl->i + 1;
+  const int nu = nu_window(i, a.mmax, ctl->truncation);
+  const int slots = a.mmax + 1;
+  const int64_t N = a.N;
+  if (threadIdx.x < nu) {
+    const int k = i - nu + (int)threadIdx.x;
+    s_off[threadIdx.x] = (size_t)(k % slots) * (size_t)N;
+  }
+  __syncthreads();
+  double acc[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) acc[j] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * kGcrThreads + threadIdx.x; e < N; e += (int64_t)gridDim.x * kGcrThreads) {
+    const double wv = __ldg(&a.w[e]);
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+      if (j < nu) acc[j] = fma(wv, __ldg(&a.S[s_off[j] + e]), acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    if (j < nu) {
+      const double v = warp_sum(acc[j]);
+      if (lane == 0) s_red[warp * nu + j] = v;
+    }
+  }
+  __syncthreads();
+  if (!combine_block_partials(s_red, nu, a.partials, NW, &ctl->counter, s_sum)) return;
+  if (threadIdx.x != 0) return;
+  // algorithmic traffic of the iteration's kernels: advance reads u, w, m, x,
+  // r and 3 nu_{i-1} history vectors, writes p, s, q, x, r, u; the walk reads
+  // u, r and the 4 coefficient arrays, writes w and t; the window pass reads w
+  // and nu_i s_k.  FP64: 3 nu_{i-1} + 3 (advance) + 7 (stencil) + 3 + nu_i FMAs, 1 sub.
+  const int nwp = ctl->nw;
+  ctl->passes += 1;
+  ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + 4 + 2) + (1 + nu));
+  ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + stencil_flops + nu + 3) + 1.0);
+  cgcr_iteration_scalars(ctl, i, nu, ctl->pend[0], ctl->pend[1], ctl->pend[2], s_sum);
+}
+
 // Fill: gamma_0 = <r_0, w_0> with w_0 = A u_0 = s_0, eta_0 = <s_0, s_0>, ||r_0||^2.
 __global__ void __launch_bounds__(kThreads) pipegcr_fill_dots(const double* __restrict__ r,
                                                               const double* __restrict__ w, int64_t N,
@@ -319,6 +413,34 @@ class PipeGcr : public Method {
     if (!env.partials_fit(dblocks, tmpl + 3)) return cudaErrorInvalidValue;
     cudaError_t e = env.mark_pass(0);
     if (e != cudaSuccess) return e;
+    if (stencil) {
+      TiledStencil<double, double> T;
+      const int slots = adv ? tiled_stencil_slots(pipegcr_apply_walk<true>, env.ctx->num_sms)
+                            : tiled_stencil_slots(pipegcr_apply_walk<false>, env.ctx->num_sms);
+      const int units = tiled_stencil_setup<double, double>(T, op, op->d, op->kx, op->ky, op->kz, slots);
+      const int64_t wcap = env.partials_cap / 3;
+      const int wblocks = (int)(units < wcap ? units : wcap);
+      const int64_t wneed = (N_ + kGcrThreads - 1) / kGcrThreads;
+      const int64_t wslots = (int64_t)env.ctx->num_sms * kWinBlocksPerSm;
+      const int sblocks = (int)(wneed < wslots ? wneed : wslots);
+      if (!env.partials_fit(sblocks, tmpl)) return cudaErrorInvalidValue;
+      switch (tmpl) {
+        case 8: pipegcr_advance<8><<<ablocks, kThreads, 0, env.st>>>(a); break;
+        case 16: pipegcr_advance<16><<<ablocks, kThreads, 0, env.st>>>(a); break;
+        default: pipegcr_advance<32><<<ablocks, kThreads, 0, env.st>>>(a); break;
+      }
+      if (adv) pipegcr_apply_walk<true><<<wblocks, kTileThreads, 0, env.st>>>(T, a);
+      else pipegcr_apply_walk<false><<<wblocks, kTileThreads, 0, env.st>>>(T, a);
+      const int sf = adv ? 10 : 7;
+      switch (tmpl) {
+        case 8: pipegcr_window_dots<8><<<sblocks, kGcrThreads, 0, env.st>>>(a, sf); break;
+        case 16: pipegcr_window_dots<16><<<sblocks, kGcrThreads, 0, env.st>>>(a, sf); break;
+        default: pipegcr_window_dots<32><<<sblocks, kGcrThreads, 0, env.st>>>(a, sf); break;
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = env.mark_pass(1)) != cudaSuccess) return e;
+      return env.pc_apply(t_, m_, u_, &env.ctl->status);   // m_i = B(w_i - r_i) + u_i
+    }
     switch (tmpl) {
       case 8:
         pipegcr_advance<8><<<ablocks, kThreads, 0, env.st>>>(a);

@@ -62,6 +62,7 @@ struct SolveCtl {
   double alg_bytes;        // their algorithmic HBM bytes
   double alg_flops;        // their FP64 flops (FMA = 2)
   double theta;            // projection coefficient <r_i, w_i>/<r_i, r_i> (eq. proj variant)
+  double pend[3];          // reduction results handed from one kernel to the next (PIPEGCR apply)
 };
 
 // Control block of a preconditioner application (inner iterations).

@@ -480,6 +480,27 @@ class Server:
         self._n[int(t.value)] = bh.size
         return int(t.value)
 
+    def submit_csr(self, rowptr, colidx, vals, b, x0=None, pc_kind="jacobi", **kw) -> int:
+        """Queues a general sparse system (CSR, host arrays) A x = b; returns the ticket."""
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(colidx, dtype=np.int32)
+        va = np.ascontiguousarray(vals, dtype=np.float64)
+        r = Request()
+        r.op.kind = OP_KINDS["csr"]
+        r.op.n, r.op.nnz = len(rp) - 1, len(va)
+        r.op.rowptr, r.op.colidx, r.op.vals, r.op.csr_on_device = rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0
+        r.pc.kind = PC_KINDS[pc_kind]
+        r.params = make_params(**kw)
+        bh = np.ascontiguousarray(b, dtype=np.float64)
+        r.b = bh.ctypes.data
+        if x0 is not None:
+            xh = np.ascontiguousarray(x0, dtype=np.float64)
+            r.x0 = xh.ctypes.data
+        t = C.c_uint64()
+        _check(load().pfk_submit(self.h, C.byref(r), C.byref(t)))
+        self._n[int(t.value)] = bh.size
+        return int(t.value)
+
     def poll(self, ticket: int, wait_ms: int = -1):
         """(x, info dict, latency_ms) once the request is done, None while pending."""
         x = np.empty(self._n[ticket])

@@ -105,3 +105,34 @@ def test_pending_poll_and_destroy_with_queued_requests(ctx):
     # the last of four sequential solves cannot be done right after submission
     assert srv.poll(tickets[-1], wait_ms=0) is None
     srv.close()   # finishes the active solve, drops the queued ones
+
+
+def test_csr_requests_and_validation(ctx):
+    """General sparse requests (the 64x64 inclusion problem assembled as CSR, with
+    Jacobi) served alongside stencil requests equal their solves alone; a CSR
+    request with inconsistent row pointers is rejected at submission."""
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson2d_inclusions()
+    rp, ci, va = _csr_arrays(c)
+    srv = pfk.Server(ctx, workers=3)
+    (r1, c1), = _requests(1, 20, 20)
+    tickets = [srv.submit_csr(rp, ci, va, c["b"], method=m, mmax=30, rtol=1e-8) for m in ("pipefcg", "pipegcr")]
+    ts = srv.submit(c1["dims"], c1["eta"], c1["b"], method="pipefcg", **KW)
+    got = [srv.poll(t) for t in tickets]
+    assert srv.poll(ts)[1]["status_name"] == "ok"
+    op = pfk.Operator.csr(ctx, rp, ci, va)
+    for (x, info, _), m in zip(got, ("pipefcg", "pipegcr")):
+        xa, ia, _ = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], method=m, mmax=30, rtol=1e-8)
+        assert info["status_name"] == ia["status_name"]
+        assert info["iterations"] == ia["iterations"]
+        assert np.array_equal(x, xa)
+    bad = rp.copy()
+    bad[-1] += 1
+    with pytest.raises(pfk.PfkError, match="row pointers"):
+        srv.submit_csr(bad, ci, va, c["b"])
+    srv.close()
+
+
+def _csr_arrays(c):
+    csr = O.StencilOperator(c["dims"], c["eta"]).to_csr()
+    return csr.rowptr, csr.colidx, csr.vals
