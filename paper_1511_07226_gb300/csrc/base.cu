@@ -7,6 +7,7 @@
 // boundary plus a last-block combine, with no host round trip.
 #include "pfk_internal.cuh"
 #include "solver.cuh"
+#include "stencil.cuh"
 
 #include <cmath>
 
@@ -193,31 +194,8 @@ __global__ void __launch_bounds__(kThreads, 3) base_maxpy(const double* __restri
 // block runs the mode's scalar step.
 enum { kApplyFcgFill = 0, kApplyFcgEta = 1, kApplyGcrFill = 2, kApplyGcrFinal = 3 };
 
-__global__ void __launch_bounds__(kThreads) base_apply_dots(StencilView A, double* __restrict__ P,
-                                                            double* __restrict__ S, const double* __restrict__ r,
-                                                            int64_t N, SolveCtl* ctl, double* partials, int mode) {
-  if (ctl->status != kRun) return;
-  const bool fill = (mode == kApplyFcgFill || mode == kApplyGcrFill);
-  const int i = fill ? 0 : ctl->i + 1;
-  const int slots = ctl->mmax + 1;
-  const size_t off = (size_t)(i % slots) * (size_t)N;
-  const double* p = P + off;
-  double* s = S + off;
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    const double sv = base_row(A, p, e);
-    s[e] = sv;
-    const double pv = p[e], rv = r[e];
-    acc[0] = fma(pv, rv, acc[0]);
-    acc[1] = fma(pv, sv, acc[1]);
-    acc[2] = fma(rv, sv, acc[2]);
-    acc[3] = fma(sv, sv, acc[3]);
-    acc[4] = fma(rv, rv, acc[4]);
-  }
-  __shared__ double s_red[(kThreads / 32) * 5];
-  __shared__ double s_sum[5];
-  if (!reduce_last_block<5>(acc, 5, partials, 5, &ctl->counter, s_red, s_sum)) return;
-  if (threadIdx.x != 0) return;
+// The scalar step after s = A p and its five dots (last block, one thread).
+__device__ __forceinline__ void base_apply_scalars(SolveCtl* ctl, int i, int slots, int mode, const double* s_sum) {
   const double pr = s_sum[0], ps = s_sum[1], rs = s_sum[2], ss = s_sum[3], rr = s_sum[4];
   if (mode == kApplyFcgFill) { cgcr_fill_scalars(ctl, pr, ps, rr); return; }        // gamma_0 = <u_0, r_0>, eta_0 = <p_0, s_0>
   if (mode == kApplyGcrFill) { cgcr_fill_scalars(ctl, rs, ss, rr); return; }        // gamma_0 = <r_0, s_0>, eta_0 = <s_0, s_0>
@@ -255,12 +233,71 @@ __global__ void __launch_bounds__(kThreads) base_apply_dots(StencilView A, doubl
   if (ctl->it >= ctl->maxit) { ctl->status = kMaxit; return; }
 }
 
-// y = A m (plain, status gated) for GCR's A u_i.
-__global__ void __launch_bounds__(kThreads) base_apply(StencilView A, const double* __restrict__ m,
-                                                       double* __restrict__ y, int64_t N, const int* status) {
-  if (*status != kRun) return;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    y[e] = base_row(A, m, e);
+__global__ void __launch_bounds__(kThreads) base_apply_dots(StencilView A, double* __restrict__ P,
+                                                            double* __restrict__ S, const double* __restrict__ r,
+                                                            int64_t N, SolveCtl* ctl, double* partials, int mode) {
+  if (ctl->status != kRun) return;
+  const bool fill = (mode == kApplyFcgFill || mode == kApplyGcrFill);
+  const int i = fill ? 0 : ctl->i + 1;
+  const int slots = ctl->mmax + 1;
+  const size_t off = (size_t)(i % slots) * (size_t)N;
+  const double* p = P + off;
+  double* s = S + off;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const double sv = base_row(A, p, e);
+    s[e] = sv;
+    const double pv = p[e], rv = r[e];
+    acc[0] = fma(pv, rv, acc[0]);
+    acc[1] = fma(pv, sv, acc[1]);
+    acc[2] = fma(rv, sv, acc[2]);
+    acc[3] = fma(sv, sv, acc[3]);
+    acc[4] = fma(rv, rv, acc[4]);
+  }
+  __shared__ double s_red[(kThreads / 32) * 5];
+  __shared__ double s_sum[5];
+  if (!reduce_last_block<5>(acc, 5, partials, 5, &ctl->counter, s_red, s_sum)) return;
+  if (threadIdx.x != 0) return;
+  base_apply_scalars(ctl, i, slots, mode, s_sum);
+}
+
+// Stencil operators: the same step on the tiled z-marching walk (s = A p and
+// the five dots in its epilogue, r prefetched one plane ahead).
+struct BaseApplyEpi {
+  double* __restrict__ s;
+  const double* __restrict__ r;
+  double acc[5];
+  struct Pre {
+    double r;
+  };
+  __device__ __forceinline__ Pre pre(int64_t c) const { return Pre{r[c]}; }
+  __device__ __forceinline__ void operator()(int64_t c, double sv, double pv, const Pre& p) {
+    s[c] = sv;
+    acc[0] = fma(pv, p.r, acc[0]);
+    acc[1] = fma(pv, sv, acc[1]);
+    acc[2] = fma(p.r, sv, acc[2]);
+    acc[3] = fma(sv, sv, acc[3]);
+    acc[4] = fma(p.r, p.r, acc[4]);
+  }
+};
+
+template <bool ADV>
+__global__ void __launch_bounds__(kTileThreads) base_apply_dots_walk(TiledStencil<double, double> T,
+                                                                     double* __restrict__ P, double* __restrict__ S,
+                                                                     const double* __restrict__ r, int64_t N,
+                                                                     SolveCtl* ctl, double* partials, int mode) {
+  if (ctl->status != kRun) return;
+  const bool fill = (mode == kApplyFcgFill || mode == kApplyGcrFill);
+  const int i = fill ? 0 : ctl->i + 1;
+  const int slots = ctl->mmax + 1;
+  const size_t off = (size_t)(i % slots) * (size_t)N;
+  BaseApplyEpi e{S + off, r, {0.0, 0.0, 0.0, 0.0, 0.0}};
+  tiled_stencil_walk<double, double, ADV, 1>(T, P + off, e);
+  __shared__ double s_red[(kTileThreads / 32) * 5];
+  __shared__ double s_sum[5];
+  if (!reduce_last_block<5>(e.acc, 5, partials, 5, &ctl->counter, s_red, s_sum)) return;
+  if (threadIdx.x != 0) return;
+  base_apply_scalars(ctl, i, slots, mode, s_sum);
 }
 
 static int base_template(int mmax) { return mmax <= 8 ? 8 : mmax <= 16 ? 16 : 32; }
@@ -290,6 +327,19 @@ static cudaError_t launch_maxpy(const SolveEnv& env, int tmpl, const double* u, 
 }
 
 static cudaError_t launch_apply_dots(const SolveEnv& env, double* P, double* S, const double* r, int mode) {
+  const pfk_operator* op = env.op;
+  if (!op->rowptr) {
+    TiledStencil<double, double> T;
+    const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
+    const int slots = adv ? tiled_stencil_slots(base_apply_dots_walk<true>, env.ctx->num_sms)
+                          : tiled_stencil_slots(base_apply_dots_walk<false>, env.ctx->num_sms);
+    const int units = tiled_stencil_setup<double, double>(T, op, op->d, op->kx, op->ky, op->kz, slots);
+    const int64_t cap = env.partials_cap / 5;
+    const int blocks = (int)(units < cap ? units : cap);
+    if (adv) base_apply_dots_walk<true><<<blocks, kTileThreads, 0, env.st>>>(T, P, S, r, env.N, env.ctl, env.partials, mode);
+    else base_apply_dots_walk<false><<<blocks, kTileThreads, 0, env.st>>>(T, P, S, r, env.N, env.ctl, env.partials, mode);
+    return cudaGetLastError();
+  }
   const int blocks = stream_blocks(env.ctx, env.N, 2);
   if (!env.partials_fit(blocks, 5)) return cudaErrorInvalidValue;
   base_apply_dots<<<blocks, kThreads, 0, env.st>>>(view_of(env.op), P, S, r, env.N, env.ctl, env.partials, mode);
@@ -362,8 +412,7 @@ class Gcr : public Method {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = env.pc_apply(r_, u_, nullptr, status)) != cudaSuccess) return e;         // u_i = B(r_i)
     if ((e = env.mark_pass(0)) != cudaSuccess) return e;
-    base_apply<<<stream_blocks(env.ctx, N_, 8), kThreads, 0, env.st>>>(view_of(env.op), u_, au_, N_, status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;                            // A u_i
+    if ((e = op_apply(env.op, u_, au_, nullptr, status, env.st)) != cudaSuccess) return e;   // A u_i
     if ((e = launch_window_dots(env, tmpl, au_, r_, S_, kDotsGcr)) != cudaSuccess) return e;  // betas
     if ((e = launch_maxpy(env, tmpl, u_, P_)) != cudaSuccess) return e;                // p_i
     if ((e = launch_apply_dots(env, P_, S_, r_, kApplyGcrFinal)) != cudaSuccess) return e;    // s_i, gamma, eta
@@ -446,6 +495,46 @@ __global__ void __launch_bounds__(kThreads) fgb_apply_store(StencilView A, const
     z[e] = base_row(A, ucur, e);
     U[off + e] = ucur[e];
   }
+}
+
+// Stencil operators: z = A u and the copy of u into U on the tiled walk.
+struct FgStoreEpi {
+  double* __restrict__ z;
+  double* __restrict__ u;
+  struct Pre {};
+  __device__ __forceinline__ Pre pre(int64_t) const { return Pre{}; }
+  __device__ __forceinline__ void operator()(int64_t c, double zv, double uv, const Pre&) const {
+    z[c] = zv;
+    u[c] = uv;
+  }
+};
+
+template <bool ADV>
+__global__ void __launch_bounds__(kTileThreads) fgb_apply_store_walk(TiledStencil<double, double> T,
+                                                                     const double* __restrict__ ucur,
+                                                                     double* __restrict__ U, double* __restrict__ z,
+                                                                     int64_t N, const FgState* gs, const int* status) {
+  if (*status != kRun) return;
+  FgStoreEpi e{z, U + (size_t)gs->k * (size_t)N};
+  tiled_stencil_walk<double, double, ADV, 1>(T, ucur, e);
+}
+
+static cudaError_t launch_apply_store(const SolveEnv& env, const double* ucur, double* U, double* z,
+                                      const FgState* gs, const int* status) {
+  const pfk_operator* op = env.op;
+  if (!op->rowptr) {
+    TiledStencil<double, double> T;
+    const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
+    const int slots = adv ? tiled_stencil_slots(fgb_apply_store_walk<true>, env.ctx->num_sms)
+                          : tiled_stencil_slots(fgb_apply_store_walk<false>, env.ctx->num_sms);
+    const int units = tiled_stencil_setup<double, double>(T, op, op->d, op->kx, op->ky, op->kz, slots);
+    if (adv) fgb_apply_store_walk<true><<<units, kTileThreads, 0, env.st>>>(T, ucur, U, z, env.N, gs, status);
+    else fgb_apply_store_walk<false><<<units, kTileThreads, 0, env.st>>>(T, ucur, U, z, env.N, gs, status);
+  } else {
+    fgb_apply_store<<<stream_blocks(env.ctx, env.N, 8), kThreads, 0, env.st>>>(view_of(op), ucur, U, z, env.N, gs,
+                                                                               status);
+  }
+  return cudaGetLastError();
 }
 
 // Classical Gram-Schmidt coefficients h_{j,k} = <p_j, z_k>, j <= k (transposed dots).
@@ -601,9 +690,7 @@ class Fgmres : public Method {
     fgb_scale<<<stream_blocks(env.ctx, N_, 8), kThreads, 0, env.st>>>(r_, P_, pcur_, N_, gs_, status);  // p_0
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = env.pc_apply(pcur_, ucur_, nullptr, status)) != cudaSuccess) return e;       // u_0 = B(p_0)
-    fgb_apply_store<<<stream_blocks(env.ctx, N_, 8), kThreads, 0, env.st>>>(view_of(env.op), ucur_, U_, z_, N_, gs_,
-                                                                            status);     // z_0 = A u_0
-    return cudaGetLastError();
+    return launch_apply_store(env, ucur_, U_, z_, gs_, status);                            // z_0 = A u_0
   }
   cudaError_t iteration(const SolveEnv& env, double* x) override {
     (void)x;
@@ -635,9 +722,7 @@ class Fgmres : public Method {
     fgb_scale<<<stream_blocks(env.ctx, N_, 8), kThreads, 0, env.st>>>(nullptr, P_, pcur_, N_, gs_, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;                              // p_k = pbar / h
     if ((e = env.pc_apply(pcur_, ucur_, nullptr, status)) != cudaSuccess) return e;    // u_k = B(p_k)
-    fgb_apply_store<<<stream_blocks(env.ctx, N_, 8), kThreads, 0, env.st>>>(view_of(env.op), ucur_, U_, z_, N_, gs_,
-                                                                            status);  // z_k = A u_k
-    return cudaGetLastError();
+    return launch_apply_store(env, ucur_, U_, z_, gs_, status);                          // z_k = A u_k
   }
   cudaError_t end_cycle(const SolveEnv& env, double* x) override {
     fgb_lsq<<<1, 32, 0, env.st>>>(gs_);
