@@ -195,7 +195,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partial sums themselves: smem[w * nd + j] holds warp w's sum of value j.
 // Writes this block's partial sums, then the last block to arrive combines all
 // blocks' partials in a fixed order into sums[j] and returns true.
-__device__ __forceinline__ bool combine_block_partials(const double* smem, int nd, double* partials, int stride,
+//
+// The combination runs on one block while the rest of the GPU idles, and its
+// loads come from L2 (~0.4 us each), so they are issued many at a time: for
+// nd <= 4 thread t takes rows t, t + T, ... (all nd values of a row, four
+// rows per step); otherwise lane l of warp w takes values l and l + 32 of
+// rows w, w + nwarps, ... (a coalesced row per load, 8 rows per step).  Each
+// thread adds its rows in increasing order, then a fixed shuffle tree (nd <=
+// 4) or the warps in order combine them: the sums are deterministic.  smem is
+// reused for the per-warp results (it holds nwarps * nd doubles).
+__device__ __forceinline__ bool combine_block_partials(double* smem, int nd, double* partials, int stride,
                                                        unsigned int* counter, double* sums) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int j = threadIdx.x; j < nd; j += blockDim.x) {
@@ -214,11 +223,67 @@ __device__ __forceinline__ bool combine_block_partials(const double* smem, int n
   if (!s_last) return false;
   __threadfence();
   const int nb = gridDim.x;
-  for (int j = warp; j < nd; j += nwarps) {
+  if (nd <= 4) {
+    const int T = blockDim.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int b = threadIdx.x;
+    for (; b + 3 * T < nb; b += 4 * T) {
+      double t[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t[u][q] = q < nd ? __ldcg(&partials[(size_t)(b + u * T) * stride + q]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += t[u][q];
+    }
+    for (; b < nb; b += T)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nd) acc[q] += __ldcg(&partials[(size_t)b * stride + q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q < nd) {
+        const double v = warp_sum(acc[q]);
+        if (lane == 0) smem[warp * nd + q] = v;
+      }
+    }
+  } else {
+    constexpr int U = 8;
+    for (int jc = 0; jc < nd; jc += 64) {
+      const int j0 = jc + lane, j1 = jc + lane + 32;
+      const bool h0 = j0 < nd, h1 = j1 < nd;
+      double a0 = 0.0, a1 = 0.0;
+      int b = warp;
+      for (; b + (U - 1) * nwarps < nb; b += U * nwarps) {
+        double t0[U], t1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const double* row = partials + (size_t)(b + u * nwarps) * stride;
+          t0[u] = h0 ? __ldcg(row + j0) : 0.0;
+          t1[u] = h1 ? __ldcg(row + j1) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          a0 += t0[u];
+          a1 += t1[u];
+        }
+      }
+      for (; b < nb; b += nwarps) {
+        const double* row = partials + (size_t)b * stride;
+        if (h0) a0 += __ldcg(row + j0);
+        if (h1) a1 += __ldcg(row + j1);
+      }
+      if (h0) smem[warp * nd + j0] = a0;
+      if (h1) smem[warp * nd + j1] = a1;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nd; j += blockDim.x) {
     double v = 0.0;
-    for (int b = lane; b < nb; b += 32) v += __ldcg(&partials[(size_t)b * stride + j]);
-    v = warp_sum(v);
-    if (lane == 0) sums[j] = v;
+    for (int w = 0; w < nwarps; ++w) v += smem[w * nd + j];
+    sums[j] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
