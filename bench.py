@@ -51,8 +51,8 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 # (profiles/pipefcg_pass_96cube.md): one full-window launch (nu = 30) on 96^3,
 # 948.19 MB read + written against 955.51 MB algorithmic, scaled to 128^3 by
 # the number of unknowns.  Valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha256": "f132cf64f45e1ba8b2e6effa03ac6c24bbc14f75b39213ea5a1deee2f178da5a",
-               "bytes_per_launch": 2.2488e9, "alg_bytes_per_launch": 2.2649e9, "window": 30,
+NCU_TRAFFIC = {"source_sha256": "037833e608cc319cac530c4397240bda08b360e0a894f56d3059fcd303fc7da8",
+               "bytes_per_launch": 2.2478e9, "alg_bytes_per_launch": 2.2649e9, "window": 30,
                "captured_on": "96^3, scaled by 128^3/96^3"}
 
 
