@@ -81,7 +81,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("pipefcg.cu", "pfk_internal.cuh"):
+    for f in ("pipefcg.cu", "pfk_internal.cuh", "solver.cuh"):
         with open(os.path.join(ROOT, "paper_1511_07226_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

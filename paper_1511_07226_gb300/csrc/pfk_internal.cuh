@@ -24,6 +24,8 @@ namespace pfk {
 constexpr int kThreads = 256;          // threads per block of the streaming kernels
 constexpr int kMaxBlocksPerSm = 8;     // upper bound of every reduction kernel's grid, per SM
 constexpr int kPartialStride = PFK_MAX_MMAX + 8;   // upper bound of values per block in a reduction
+constexpr int kCombineGroup = 32;      // blocks per group of the two-level combine
+constexpr int kMaxCombineGroups = 64;  // groups it supports (grids of up to 2,048 blocks)
 
 // Status codes kept in SolveCtl::status.
 enum DevStatus : int {
@@ -58,6 +60,7 @@ struct SolveCtl {
   double eta_ring[PFK_MAX_MMAX + 1];
   double* history;         // device buffer hist_cap * PFK_HISTORY_FIELDS
   unsigned int counter;    // arrival counter of the last-block reduction
+  unsigned int gcounter[kMaxCombineGroups];   // per-group arrival counters of the two-level combine
   int passes;              // fused passes that did work
   double alg_bytes;        // their algorithmic HBM bytes
   double alg_flops;        // their FP64 flops (FMA = 2)
@@ -191,57 +194,37 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Second half of reduce_last_block, for kernels that prepare the per-warp
-// partial sums themselves: smem[w * nd + j] holds warp w's sum of value j.
-// Writes this block's partial sums, then the last block to arrive combines all
-// blocks' partials in a fixed order into sums[j] and returns true.
-//
-// The combination runs on one block while the rest of the GPU idles, and its
-// loads come from L2 (~0.4 us each), so they are issued many at a time: for
-// nd <= 4 thread t takes rows t, t + T, ... (all nd values of a row, four
-// rows per step); otherwise lane l of warp w takes values l and l + 32 of
-// rows w, w + nwarps, ... (a coalesced row per load, 8 rows per step).  Each
+// sums over rows: out[j] = sum_{b < nrows} rows[b * stride + j], j < nd, by
+// all threads of the block.  The loads come from L2 (~0.4 us each) while the
+// rest of the GPU may idle, so they are issued many at a time: for nd <= 4
+// thread t takes rows t, t + T, ... (all nd values of a row, four rows per
+// step); otherwise lane l of warp w takes values l and l + 32 of rows w,
+// w + nwarps, ... (a coalesced row per load, eight rows per step).  Each
 // thread adds its rows in increasing order, then a fixed shuffle tree (nd <=
-// 4) or the warps in order combine them: the sums are deterministic.  smem is
-// reused for the per-warp results (it holds nwarps * nd doubles).
-__device__ __forceinline__ bool combine_block_partials(double* smem, int nd, double* partials, int stride,
-                                                       unsigned int* counter, double* sums) {
+// 4) or the warps in order combine them: the sums are deterministic.  smem
+// holds nwarps * nd doubles; out may be shared or global memory.
+__device__ __forceinline__ void sum_rows(const double* rows, int nrows, int nd, int stride, double* smem,
+                                         double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int j = threadIdx.x; j < nd; j += blockDim.x) {
-    double v = 0.0;
-    for (int w = 0; w < nwarps; ++w) v += smem[w * nd + j];
-    partials[(size_t)blockIdx.x * stride + j] = v;
-  }
-  __shared__ unsigned int s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int prev = atomicAdd(counter, 1u);
-    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (!s_last) return false;
-  __threadfence();
-  const int nb = gridDim.x;
   if (nd <= 4) {
     const int T = blockDim.x;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int b = threadIdx.x;
-    for (; b + 3 * T < nb; b += 4 * T) {
+    for (; b + 3 * T < nrows; b += 4 * T) {
       double t[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) t[u][q] = q < nd ? __ldcg(&partials[(size_t)(b + u * T) * stride + q]) : 0.0;
+        for (int q = 0; q < 4; ++q) t[u][q] = q < nd ? __ldcg(&rows[(size_t)(b + u * T) * stride + q]) : 0.0;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += t[u][q];
     }
-    for (; b < nb; b += T)
+    for (; b < nrows; b += T)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (q < nd) acc[q] += __ldcg(&partials[(size_t)b * stride + q]);
+        if (q < nd) acc[q] += __ldcg(&rows[(size_t)b * stride + q]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (q < nd) {
@@ -256,11 +239,11 @@ __device__ __forceinline__ bool combine_block_partials(double* smem, int nd, dou
       const bool h0 = j0 < nd, h1 = j1 < nd;
       double a0 = 0.0, a1 = 0.0;
       int b = warp;
-      for (; b + (U - 1) * nwarps < nb; b += U * nwarps) {
+      for (; b + (U - 1) * nwarps < nrows; b += U * nwarps) {
         double t0[U], t1[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const double* row = partials + (size_t)(b + u * nwarps) * stride;
+          const double* row = rows + (size_t)(b + u * nwarps) * stride;
           t0[u] = h0 ? __ldcg(row + j0) : 0.0;
           t1[u] = h1 ? __ldcg(row + j1) : 0.0;
         }
@@ -270,8 +253,8 @@ __device__ __forceinline__ bool combine_block_partials(double* smem, int nd, dou
           a1 += t1[u];
         }
       }
-      for (; b < nb; b += nwarps) {
-        const double* row = partials + (size_t)b * stride;
+      for (; b < nrows; b += nwarps) {
+        const double* row = rows + (size_t)b * stride;
         if (h0) a0 += __ldcg(row + j0);
         if (h1) a1 += __ldcg(row + j1);
       }
@@ -283,9 +266,72 @@ __device__ __forceinline__ bool combine_block_partials(double* smem, int nd, dou
   for (int j = threadIdx.x; j < nd; j += blockDim.x) {
     double v = 0.0;
     for (int w = 0; w < nwarps; ++w) v += smem[w * nd + j];
-    sums[j] = v;
+    out[j] = v;
   }
   __syncthreads();
+}
+
+// Writes this block's row partials[blockIdx.x * stride + j] = sum_w smem[w *
+// nd + j] (smem[w * nd + j]: warp w's sum of value j).
+__device__ __forceinline__ void write_block_row(const double* smem, int nd, double* partials, int stride) {
+  const int nwarps = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += smem[w * nd + j];
+    partials[(size_t)blockIdx.x * stride + j] = v;
+  }
+}
+
+// Arrival at `counter` after this block's writes; true in the block that
+// arrives as number `count` (all its threads), which then sees every earlier
+// arrival's writes.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int count) {
+  __shared__ unsigned int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == count - 1) ? 1u : 0u;
+  __syncthreads();
+  const bool last = s_last != 0u;
+  if (last) __threadfence();
+  return last;
+}
+
+// Second half of reduce_last_block, for kernels that prepare the per-warp
+// partial sums themselves: smem[w * nd + j] holds warp w's sum of value j.
+// Writes this block's partial sums, then the last block to arrive combines all
+// blocks' partials in a fixed order (sum_rows) into sums[j] and returns true.
+// smem is reused.
+__device__ __forceinline__ bool combine_block_partials(double* smem, int nd, double* partials, int stride,
+                                                       unsigned int* counter, double* sums) {
+  write_block_row(smem, nd, partials, stride);
+  if (!arrive_last(counter, gridDim.x)) return false;
+  sum_rows(partials, gridDim.x, nd, stride, smem, sums);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// Two-level variant for the large reductions: the last block of each group of
+// kCombineGroup consecutive blocks sums the group's rows (sum_rows, block
+// order) into group row nb + g while other blocks still compute; the last
+// group to finish sums the group rows in group order into sums.  The serial
+// tail is one group's rows plus the group rows instead of all nb rows.
+// partials holds (nb + ceil(nb / kCombineGroup)) * stride doubles; gcounter
+// one zero counter per group (left zero); nb <= kCombineGroup *
+// kMaxCombineGroups.
+__device__ __forceinline__ bool combine_block_partials_2l(double* smem, int nd, double* partials, int stride,
+                                                          unsigned int* counter, unsigned int* gcounter,
+                                                          double* sums) {
+  const int nb = gridDim.x;
+  const int g = blockIdx.x / kCombineGroup;
+  const int gb0 = g * kCombineGroup;
+  const int gn = min(kCombineGroup, nb - gb0);
+  const int ng = (nb + kCombineGroup - 1) / kCombineGroup;
+  write_block_row(smem, nd, partials, stride);
+  if (!arrive_last(&gcounter[g], (unsigned int)gn)) return false;
+  sum_rows(partials + (size_t)gb0 * stride, gn, nd, stride, smem, partials + (size_t)(nb + g) * stride);
+  if (threadIdx.x == 0) gcounter[g] = 0u;
+  if (!arrive_last(counter, (unsigned int)ng)) return false;
+  sum_rows(partials + (size_t)nb * stride, ng, nd, stride, smem, sums);
   if (threadIdx.x == 0) *counter = 0u;
   return true;
 }

@@ -185,25 +185,31 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSm) pipefcg_pass(F
     if (lane < nwp) s_red[warp * nd + 4 + lane] = gw;
     __syncthreads();
   }
-  if (!combine_block_partials(s_red, nwp + 4 + (a.theta ? 1 : 0), a.partials, ND, &ctl->counter, s_sum)) return;
-  if (threadIdx.x != 0) return;
+  if (!combine_block_partials_2l(s_red, nwp + 4 + (a.theta ? 1 : 0), a.partials, ND, &ctl->counter, ctl->gcounter,
+                                 s_sum))
+    return;
 
-  // ---- scalar phase of iteration i (one thread) ----
+  // ---- scalar phase of iteration i (the last block; s_red is free again) ----
   const int i = iprev + 1;
   const double gamma = s_sum[0], delta = s_sum[1], rr = s_sum[2];
-  // algorithmic traffic of this pass: u, w, m, n, x, r and 4 nu_{i-1} history
-  // vectors read; p, s, q, z, x, r, u, w (and t) written.  FP64 flops: 4 nu
-  // MAXPY FMAs, 4 advance FMAs, nu + 4 dot FMAs, and the subtraction for t.
-  ctl->passes += 1;
-  ctl->alg_bytes += 8.0 * (double)N * (double)(4 * nwp + 14 + ((a.naive || a.theta) ? 0 : 1));
-  ctl->alg_flops += (double)N * (2.0 * (5 * nwp + 8 + (a.theta ? 1 : 0)) + ((a.naive || a.theta) ? 0.0 : 1.0));
-  if (a.theta) ctl->theta = rr > 0.0 ? s_sum[4 + nwp] / rr : 1.0;
+  if (threadIdx.x == 0) {
+    // algorithmic traffic of this pass: u, w, m, n, x, r and 4 nu_{i-1} history
+    // vectors read; p, s, q, z, x, r, u, w (and t) written.  FP64 flops: 4 nu
+    // MAXPY FMAs, 4 advance FMAs, nu + 4 dot FMAs, and the subtraction for t.
+    ctl->passes += 1;
+    ctl->alg_bytes += 8.0 * (double)N * (double)(4 * nwp + 14 + ((a.naive || a.theta) ? 0 : 1));
+    ctl->alg_flops += (double)N * (2.0 * (5 * nwp + 8 + (a.theta ? 1 : 0)) + ((a.naive || a.theta) ? 0.0 : 1.0));
+    if (a.theta) ctl->theta = rr > 0.0 ? s_sum[4 + nwp] / rr : 1.0;
+  }
   const int nu = nu_window(i, a.mmax, ctl->truncation);
   // window dots in order k = i-1-nwp .. i-1 (W_{i-1}, then s_{i-1}); W_i is
   // the last nu of them
-  double cw[PFK_MAX_MMAX + 1];
-  for (int src = 0; src <= nwp; ++src) cw[src] = src < nwp ? s_sum[4 + src] : s_sum[3];
-  cgcr_iteration_scalars(ctl, i, nu, gamma, delta, rr, cw + (nwp + 1 - nu));
+  static_assert(NWARPS * ND >= 3 * NW + 2, "scalar-phase scratch fits in s_red");
+  double* s_cw = s_red;              // NW + 1 window dots
+  double* s_tmp = s_red + NW + 1;    // 2 NW + 1
+  if ((int)threadIdx.x <= nwp) s_cw[threadIdx.x] = (int)threadIdx.x < nwp ? s_sum[4 + threadIdx.x] : s_sum[3];
+  __syncthreads();
+  cgcr_iteration_scalars_block(ctl, i, nu, gamma, delta, rr, s_cw + (nwp + 1 - nu), s_tmp, NW);
 }
 
 // Pipeline fill dots: gamma_0 = <u_0, r_0>, delta_0 = <u_0, w_0>, ||r_0||^2,
@@ -309,7 +315,10 @@ class PipeFcg : public Method {
     const int64_t need = (N_ + kPassThreads - 1) / kPassThreads;
     const int64_t cap = (int64_t)env.ctx->num_sms * kPassBlocksPerSm;
     const int blocks = (int)(need < cap ? need : cap);
-    if (!env.partials_fit(blocks, tmpl + 5)) return cudaErrorInvalidValue;
+    // block rows plus the two-level combine's group rows
+    if (!env.partials_fit(blocks + (blocks + kCombineGroup - 1) / kCombineGroup, tmpl + 5) ||
+        blocks > kCombineGroup * kMaxCombineGroups)
+      return cudaErrorInvalidValue;
     e = launch_pass_any(a, tmpl, blocks, env.st);
     if (e != cudaSuccess) return e;
     if ((e = env.mark_pass(1)) != cudaSuccess) return e;

@@ -151,4 +151,57 @@ __device__ __forceinline__ void cgcr_iteration_scalars(SolveCtl* ctl, int i, int
   if (ctl->it >= ctl->maxit) { ctl->status = kMaxit; return; }
 }
 
+// cgcr_iteration_scalars by all threads of the (last) block: the nu window
+// betas -c_k / eta_k (each a global load of eta_k and a division) are formed
+// in parallel, one per thread, and thread 0 accumulates eta_i in the same k
+// order; everything else is thread 0's, in the same statement order.  c is
+// the window's dots in k order (shared or global memory); s_tmp holds 2 * cap
+// + 1 doubles of shared memory, cap >= nu.
+__device__ __forceinline__ void cgcr_iteration_scalars_block(SolveCtl* ctl, int i, int nu, double gamma, double delta,
+                                                             double rr, const double* c, double* s_tmp, int cap) {
+  int* s_go = (int*)(s_tmp + 2 * cap);
+  if (threadIdx.x == 0) {
+    ctl->it += 1;
+    ctl->i = i;
+    ctl->gamma = gamma;
+    ctl->delta = delta;
+    const double rnorm = sqrt(rr);
+    const double rho = cgcr_rho(ctl, gamma, rr);
+    ctl->rho = rho;
+    s_go[1] = ctl->hist_len;
+    push_history(ctl, rho, rnorm, nan(""), nan(""));
+    s_go[0] = 1;
+    if (!isfinite(rho)) { ctl->status = kNonFinite; s_go[0] = 0; }
+    else if (rho <= ctl->target) { ctl->status = kConverged; s_go[0] = 0; }
+  }
+  __syncthreads();
+  if (!s_go[0]) return;
+  const int slots = ctl->mmax + 1;
+  if ((int)threadIdx.x < nu) {
+    const int k = i - nu + (int)threadIdx.x;
+    const double ek = ctl->eta_ring[k % slots];
+    const double b = -c[threadIdx.x] / ek;
+    ctl->beta[threadIdx.x] = b;
+    s_tmp[threadIdx.x] = b * b;
+    s_tmp[cap + threadIdx.x] = ek;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double sumb = 0.0;
+  for (int jj = 0; jj < nu; ++jj) sumb = fma(s_tmp[jj], s_tmp[cap + jj], sumb);
+  const double eta = delta - sumb;
+  const double al = eta != 0.0 ? gamma / eta : nan("");
+  const int hslot = s_go[1];
+  ctl->eta = eta;
+  ctl->alpha = al;
+  ctl->nw = nu;
+  ctl->eta_ring[i % slots] = eta;
+  if (ctl->history && hslot < ctl->hist_cap) {
+    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 2] = eta;
+    ctl->history[(size_t)hslot * PFK_HISTORY_FIELDS + 3] = al;
+  }
+  if (eta <= 0.0) { ctl->status = kBreakdown; return; }
+  if (ctl->it >= ctl->maxit) { ctl->status = kMaxit; return; }
+}
+
 }  // namespace pfk
