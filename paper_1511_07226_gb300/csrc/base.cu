@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBaseThreads, kBaseBlocksPerSm) base_window_do
     if (lane < nu) s_red[warp * nd + 2 + lane] = gw;
     __syncthreads();
   }
-  if (!combine_block_partials(s_red, nu + 2, partials, ND, &ctl->counter, s_sum)) return;
+  if (!combine_block_partials_2l(s_red, nu + 2, partials, ND, &ctl->counter, ctl->gcounter, s_sum)) return;
   if (threadIdx.x != 0) return;
   const double* c = s_sum + 2;
   if (mode == kDotsFcg) {
@@ -307,7 +307,7 @@ static cudaError_t launch_window_dots(const SolveEnv& env, int tmpl, const doubl
   const int64_t need = (env.N + kBaseThreads - 1) / kBaseThreads;
   const int64_t cap = (int64_t)env.ctx->num_sms * kBaseBlocksPerSm;
   const int blocks = (int)(need < cap ? need : cap);
-  if (!env.partials_fit(blocks, tmpl + 2)) return cudaErrorInvalidValue;
+  if (!env.partials_fit_2l(blocks, tmpl + 2)) return cudaErrorInvalidValue;
   switch (tmpl) {
     case 8: base_window_dots<8><<<blocks, kBaseThreads, 0, env.st>>>(v, r, S, env.N, env.ctl, env.partials, mode); break;
     case 16: base_window_dots<16><<<blocks, kBaseThreads, 0, env.st>>>(v, r, S, env.N, env.ctl, env.partials, mode); break;
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kBaseThreads, kBaseBlocksPerSm) fgb_dots(const
   }
   if (lane < nk) s_red[warp * nk + lane] = gw;
   __syncthreads();
-  if (!combine_block_partials(s_red, nk, partials, ND, &ctl->counter, s_sum)) return;
+  if (!combine_block_partials_2l(s_red, nk, partials, ND, &ctl->counter, ctl->gcounter, s_sum)) return;
   if (threadIdx.x != 0) return;
   for (int j = 0; j < nk; ++j) gs->H[j * kGm + gs->k] = s_sum[j];
 }
@@ -700,7 +700,7 @@ class Fgmres : public Method {
     const int64_t cap = (int64_t)env.ctx->num_sms * kBaseBlocksPerSm;
     const int dblocks = (int)(need < cap ? need : cap);
     const int oblocks = stream_blocks(env.ctx, N_, 2);
-    if (!env.partials_fit(dblocks, tmpl) || !env.partials_fit(oblocks, 1)) return cudaErrorInvalidValue;
+    if (!env.partials_fit_2l(dblocks, tmpl) || !env.partials_fit(oblocks, 1)) return cudaErrorInvalidValue;
     cudaError_t e;
     if ((e = env.mark_pass(0)) != cudaSuccess) return e;
     switch (tmpl) {

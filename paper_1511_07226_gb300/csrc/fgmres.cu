@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kFgThreads, kFgBlocksPerSm) fgmres_pass(FgArgs
     if (lane < k) s_red[warp * nd + 1 + lane] = gw;
     __syncthreads();
   }
-  if (!combine_block_partials(s_red, k + 2, a.partials, ND, &ctl->counter, s_sum)) return;
+  if (!combine_block_partials_2l(s_red, k + 2, a.partials, ND, &ctl->counter, ctl->gcounter, s_sum)) return;
   if (threadIdx.x != 0) return;
   // traffic: zbar_{k-1}, qbar, wbar and 3k window vectors read, p_k, u_k,
   // zbar_k written; FP64: 3k MAXPY FMAs, 3 scalings, k + 2 dot FMAs
@@ -372,7 +372,7 @@ class PipeFgmres : public Method {
     const int64_t need = (N_ + kFgThreads - 1) / kFgThreads;
     const int64_t cap = (int64_t)env.ctx->num_sms * kFgBlocksPerSm;
     const int blocks = (int)(need < cap ? need : cap);
-    if (!env.partials_fit(blocks, tmpl + 2)) return cudaErrorInvalidValue;
+    if (!env.partials_fit_2l(blocks, tmpl + 2)) return cudaErrorInvalidValue;
     cudaError_t e = env.mark_pass(0);
     if (e != cudaSuccess) return e;
     switch (tmpl) {

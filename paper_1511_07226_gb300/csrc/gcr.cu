@@ -239,17 +239,19 @@ __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_do
     if (lane < nu) s_red[warp * nd + 3 + lane] = gw;
     __syncthreads();
   }
-  if (!combine_block_partials(s_red, nu + 3, a.partials, ND, &ctl->counter, s_sum)) return;
-  if (threadIdx.x != 0) return;
-  // algorithmic traffic of the iteration's two kernels: advance reads u, w, m,
-  // x, r and 3 nu_{i-1} history vectors, writes p, s, q, x, r, u; the apply
-  // reads u, r, the operator (4 coefficient arrays for a stencil) and nu_i s_k,
-  // writes w and t.  FP64: 3 nu_{i-1} + 3 + 7 (stencil) + nu_i + 3 FMAs, 1 sub.
-  const int nwp = ctl->nw;
-  ctl->passes += 1;
-  ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + (STENCIL ? 4 : 0) + nu + 2));
-  ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + (STENCIL ? 7 : 0) + nu + 3) + 1.0);
-  cgcr_iteration_scalars(ctl, i, nu, s_sum[0], s_sum[1], s_sum[2], s_sum + 3);
+  if (!combine_block_partials_2l(s_red, nu + 3, a.partials, ND, &ctl->counter, ctl->gcounter, s_sum)) return;
+  if (threadIdx.x == 0) {
+    // algorithmic traffic of the iteration's two kernels: advance reads u, w, m,
+    // x, r and 3 nu_{i-1} history vectors, writes p, s, q, x, r, u; the apply
+    // reads u, r, the operator (4 coefficient arrays for a stencil) and nu_i s_k,
+    // writes w and t.  FP64: 3 nu_{i-1} + 3 + 7 (stencil) + nu_i + 3 FMAs, 1 sub.
+    const int nwp = ctl->nw;
+    ctl->passes += 1;
+    ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + (STENCIL ? 4 : 0) + nu + 2));
+    ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + (STENCIL ? 7 : 0) + nu + 3) + 1.0);
+  }
+  static_assert(NWARPS * ND >= 2 * NW + 1, "scalar-phase scratch fits in s_red");
+  cgcr_iteration_scalars_block(ctl, i, nu, s_sum[0], s_sum[1], s_sum[2], s_sum + 3, s_red, NW);
 }
 
 // ---- stencil operators: w = A u by the tiled walk, then the window dots ----
@@ -329,17 +331,19 @@ __global__ void __launch_bounds__(kGcrThreads, kWinBlocksPerSm) pipegcr_window_d
     }
   }
   __syncthreads();
-  if (!combine_block_partials(s_red, nu, a.partials, NW, &ctl->counter, s_sum)) return;
-  if (threadIdx.x != 0) return;
-  // algorithmic traffic of the iteration's kernels: advance reads u, w, m, x,
-  // r and 3 nu_{i-1} history vectors, writes p, s, q, x, r, u; the walk reads
-  // u, r and the 4 coefficient arrays, writes w and t; the window pass reads w
-  // and nu_i s_k.  FP64: 3 nu_{i-1} + 3 (advance) + 7 (stencil) + 3 + nu_i FMAs, 1 sub.
-  const int nwp = ctl->nw;
-  ctl->passes += 1;
-  ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + 4 + 2) + (1 + nu));
-  ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + stencil_flops + nu + 3) + 1.0);
-  cgcr_iteration_scalars(ctl, i, nu, ctl->pend[0], ctl->pend[1], ctl->pend[2], s_sum);
+  if (!combine_block_partials_2l(s_red, nu, a.partials, NW, &ctl->counter, ctl->gcounter, s_sum)) return;
+  if (threadIdx.x == 0) {
+    // algorithmic traffic of the iteration's kernels: advance reads u, w, m, x,
+    // r and 3 nu_{i-1} history vectors, writes p, s, q, x, r, u; the walk reads
+    // u, r and the 4 coefficient arrays, writes w and t; the window pass reads w
+    // and nu_i s_k.  FP64: 3 nu_{i-1} + 3 (advance) + 7 (stencil) + 3 + nu_i FMAs, 1 sub.
+    const int nwp = ctl->nw;
+    ctl->passes += 1;
+    ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + 4 + 2) + (1 + nu));
+    ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + stencil_flops + nu + 3) + 1.0);
+  }
+  static_assert(NWARPS * NW >= 2 * NW + 1, "scalar-phase scratch fits in s_red");
+  cgcr_iteration_scalars_block(ctl, i, nu, ctl->pend[0], ctl->pend[1], ctl->pend[2], s_sum, s_red, NW);
 }
 
 // Fill: gamma_0 = <r_0, w_0> with w_0 = A u_0 = s_0, eta_0 = <s_0, s_0>, ||r_0||^2.
@@ -410,7 +414,7 @@ class PipeGcr : public Method {
     const int64_t need = (chunks + kGcrThreads / 32 - 1) / (kGcrThreads / 32);
     const int64_t cap = (int64_t)env.ctx->num_sms * kGcrBlocksPerSm;
     const int dblocks = (int)(need < cap ? need : cap);
-    if (!env.partials_fit(dblocks, tmpl + 3)) return cudaErrorInvalidValue;
+    if (!env.partials_fit_2l(dblocks, tmpl + 3)) return cudaErrorInvalidValue;
     cudaError_t e = env.mark_pass(0);
     if (e != cudaSuccess) return e;
     if (stencil) {
@@ -423,7 +427,7 @@ class PipeGcr : public Method {
       const int64_t wneed = (N_ + kGcrThreads - 1) / kGcrThreads;
       const int64_t wslots = (int64_t)env.ctx->num_sms * kWinBlocksPerSm;
       const int sblocks = (int)(wneed < wslots ? wneed : wslots);
-      if (!env.partials_fit(sblocks, tmpl)) return cudaErrorInvalidValue;
+      if (!env.partials_fit_2l(sblocks, tmpl)) return cudaErrorInvalidValue;
       switch (tmpl) {
         case 8: pipegcr_advance<8><<<ablocks, kThreads, 0, env.st>>>(a); break;
         case 16: pipegcr_advance<16><<<ablocks, kThreads, 0, env.st>>>(a); break;

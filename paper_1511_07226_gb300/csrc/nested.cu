@@ -136,7 +136,7 @@ pfk_status create_nested_pc(pfk_context* ctx, const pfk_operator* K, const pfk_o
   const int64_t wd = S->M->workspace_doubles(nu, inner->mmax);
   PFK_CUDA(ctx, cudaMallocAsync((void**)&S->ws, (size_t)wd * sizeof(double), st));
   S->M->bind(S->ws, nu, inner->mmax);
-  S->partials_cap = (int64_t)ctx->num_sms * kMaxBlocksPerSm * kPartialStride;
+  S->partials_cap = ((int64_t)ctx->num_sms * kMaxBlocksPerSm + kMaxCombineGroups) * kPartialStride;
   PFK_CUDA(ctx, cudaMallocAsync((void**)&S->partials, (size_t)S->partials_cap * sizeof(double), st));
   PFK_CUDA(ctx, cudaMallocAsync((void**)&S->ctl, sizeof(SolveCtl), st));
   SolveCtl c;

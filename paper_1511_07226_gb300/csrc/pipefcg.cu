@@ -315,10 +315,7 @@ class PipeFcg : public Method {
     const int64_t need = (N_ + kPassThreads - 1) / kPassThreads;
     const int64_t cap = (int64_t)env.ctx->num_sms * kPassBlocksPerSm;
     const int blocks = (int)(need < cap ? need : cap);
-    // block rows plus the two-level combine's group rows
-    if (!env.partials_fit(blocks + (blocks + kCombineGroup - 1) / kCombineGroup, tmpl + 5) ||
-        blocks > kCombineGroup * kMaxCombineGroups)
-      return cudaErrorInvalidValue;
+    if (!env.partials_fit_2l(blocks, tmpl + 5)) return cudaErrorInvalidValue;
     e = launch_pass_any(a, tmpl, blocks, env.st);
     if (e != cudaSuccess) return e;
     if ((e = env.mark_pass(1)) != cudaSuccess) return e;

@@ -148,7 +148,8 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
   // partials: room for any kernel of the solve (at most kMaxBlocksPerSm blocks
   // per SM, at most kPartialStride values per block); launches check it.
   const int64_t wd = M->workspace_doubles(N, mmax);
-  const int64_t pd = (int64_t)ctx->num_sms * kMaxBlocksPerSm * kPartialStride;
+  // block rows of the largest reduction grid plus the two-level combine's group rows
+  const int64_t pd = ((int64_t)ctx->num_sms * kMaxBlocksPerSm + kMaxCombineGroups) * kPartialStride;
   const int64_t sd = 64;
   const int hist_cap = prm->history ? prm->history_capacity : 0;
   const int64_t hd = (int64_t)hist_cap * PFK_HISTORY_FIELDS;

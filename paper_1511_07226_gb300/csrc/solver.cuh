@@ -18,6 +18,11 @@ struct SolveEnv {
 
   // True if a launch of `blocks` blocks writing `stride` partials each fits.
   bool partials_fit(int blocks, int stride) const { return (int64_t)blocks * stride <= partials_cap; }
+  // The same for a two-level combine (block rows plus one row per group).
+  bool partials_fit_2l(int blocks, int stride) const {
+    return blocks <= kCombineGroup * kMaxCombineGroups &&
+           (int64_t)(blocks + (blocks + kCombineGroup - 1) / kCombineGroup) * stride <= partials_cap;
+  }
   cudaEvent_t pass_ev0, pass_ev1;   // profiling: recorded around the fused pass (or null)
 
   // out = add + B(v); B = identity when pc is null.
