@@ -18,49 +18,23 @@ constexpr int kBaseBlocksPerSm = 6;
 constexpr int kBaseStride = kBaseThreads + 1;
 static_assert(kBaseBlocksPerSm <= kMaxBlocksPerSm, "partials are sized for kMaxBlocksPerSm blocks per SM");
 
-struct StencilView {
-  const double* d;
-  const double* kx;
-  const double* ky;
-  const double* kz;
-  int nx, ny, nz, ndim;
-  double a0, a1, a2;
-  int u0, u1, u2;
+// A CSR operator (stencil operators take the tiled walk).
+struct CsrView {
   const int32_t* rowptr;
   const int32_t* colidx;
   const double* vals;
 };
 
-static StencilView view_of(const pfk_operator* op) {
-  StencilView A;
-  A.d = op->d; A.kx = op->kx; A.ky = op->ky; A.kz = op->kz;
-  A.nx = op->nx; A.ny = op->ny; A.nz = op->nz; A.ndim = op->ndim;
-  A.a0 = op->adv[0]; A.a1 = op->adv[1]; A.a2 = op->adv[2];
-  A.u0 = op->upw[0]; A.u1 = op->upw[1]; A.u2 = op->upw[2];
+static CsrView csr_of(const pfk_operator* op) {
+  CsrView A;
   A.rowptr = op->rowptr; A.colidx = op->colidx; A.vals = op->vals;
   return A;
 }
 
-// (A m)_c for element c (stencil or CSR), the stencil's (i, j, k) from c.
-__device__ __forceinline__ double base_row(const StencilView& A, const double* __restrict__ m, int64_t c) {
-  if (A.rowptr) {
-    double acc = 0.0;
-    for (int32_t p = A.rowptr[c]; p < A.rowptr[c + 1]; ++p) acc = fma(A.vals[p], m[A.colidx[p]], acc);
-    return acc;
-  }
-  const int64_t sxy = (int64_t)A.nx * A.ny;
-  const int64_t row = c / A.nx;
-  const int i = (int)(c - row * A.nx);
-  const int j = (int)(row % A.ny), k = (int)(row / A.ny);
-  double acc = A.d[c] * m[c];
-  if (i > 0) acc = fma(-(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)), m[c - 1], acc);
-  if (i < A.nx - 1) acc = fma(-(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)), m[c + 1], acc);
-  if (j > 0) acc = fma(-(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)), m[c - A.nx], acc);
-  if (j < A.ny - 1) acc = fma(-(A.ky[c] + (A.u1 == 1 ? A.a1 : 0.0)), m[c + A.nx], acc);
-  if (A.ndim == 3) {
-    if (k > 0) acc = fma(-(A.kz[c - sxy] + (A.u2 == -1 ? A.a2 : 0.0)), m[c - sxy], acc);
-    if (k < A.nz - 1) acc = fma(-(A.kz[c] + (A.u2 == 1 ? A.a2 : 0.0)), m[c + sxy], acc);
-  }
+// (A m)_r of a CSR operator.
+__device__ __forceinline__ double base_row(const CsrView& A, const double* __restrict__ m, int64_t r) {
+  double acc = 0.0;
+  for (int32_t p = A.rowptr[r]; p < A.rowptr[r + 1]; ++p) acc = fma(A.vals[p], m[A.colidx[p]], acc);
   return acc;
 }
 
@@ -233,7 +207,8 @@ __device__ __forceinline__ void base_apply_scalars(SolveCtl* ctl, int i, int slo
   if (ctl->it >= ctl->maxit) { ctl->status = kMaxit; return; }
 }
 
-__global__ void __launch_bounds__(kThreads) base_apply_dots(StencilView A, double* __restrict__ P,
+// CSR operators: one row per thread.
+__global__ void __launch_bounds__(kThreads) base_apply_dots(CsrView A, double* __restrict__ P,
                                                             double* __restrict__ S, const double* __restrict__ r,
                                                             int64_t N, SolveCtl* ctl, double* partials, int mode) {
   if (ctl->status != kRun) return;
@@ -342,7 +317,7 @@ static cudaError_t launch_apply_dots(const SolveEnv& env, double* P, double* S, 
   }
   const int blocks = stream_blocks(env.ctx, env.N, 2);
   if (!env.partials_fit(blocks, 5)) return cudaErrorInvalidValue;
-  base_apply_dots<<<blocks, kThreads, 0, env.st>>>(view_of(env.op), P, S, r, env.N, env.ctl, env.partials, mode);
+  base_apply_dots<<<blocks, kThreads, 0, env.st>>>(csr_of(env.op), P, S, r, env.N, env.ctl, env.partials, mode);
   return cudaGetLastError();
 }
 
@@ -485,8 +460,8 @@ __global__ void __launch_bounds__(kThreads) fgb_scale(const double* __restrict__
   }
 }
 
-// z = A u_k, and u_k stored in slot k of U.
-__global__ void __launch_bounds__(kThreads) fgb_apply_store(StencilView A, const double* __restrict__ ucur,
+// z = A u_k, and u_k stored in slot k of U (CSR operators).
+__global__ void __launch_bounds__(kThreads) fgb_apply_store(CsrView A, const double* __restrict__ ucur,
                                                             double* __restrict__ U, double* __restrict__ z, int64_t N,
                                                             const FgState* gs, const int* status) {
   if (*status != kRun) return;
@@ -531,7 +506,7 @@ static cudaError_t launch_apply_store(const SolveEnv& env, const double* ucur, d
     if (adv) fgb_apply_store_walk<true><<<units, kTileThreads, 0, env.st>>>(T, ucur, U, z, env.N, gs, status);
     else fgb_apply_store_walk<false><<<units, kTileThreads, 0, env.st>>>(T, ucur, U, z, env.N, gs, status);
   } else {
-    fgb_apply_store<<<stream_blocks(env.ctx, env.N, 8), kThreads, 0, env.st>>>(view_of(op), ucur, U, z, env.N, gs,
+    fgb_apply_store<<<stream_blocks(env.ctx, env.N, 8), kThreads, 0, env.st>>>(csr_of(op), ucur, U, z, env.N, gs,
                                                                                status);
   }
   return cudaGetLastError();

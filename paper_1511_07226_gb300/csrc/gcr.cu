@@ -85,50 +85,13 @@ __global__ void __launch_bounds__(kThreads, 3) pipegcr_advance(GcrArgs a) {
   }
 }
 
-// Operator row value (A u)_c for the stencil (row-chunk mapping) or CSR.
+// Operator row value (A u)_r of a CSR operator (stencils take the tiled walk
+// below).
 struct OpView {
-  // stencil
-  const double* d;
-  const double* kx;
-  const double* ky;
-  const double* kz;
-  int nx, ny, nz, ndim;
-  double a0, a1, a2;
-  int u0, u1, u2;
-  // CSR
   const int32_t* rowptr;
   const int32_t* colidx;
   const double* vals;
 };
-
-// ADV = false (no advection): the upwind additions are zero and are not
-// evaluated (an FP64 add per neighbour saved).
-template <bool ADV>
-__device__ __forceinline__ double op_row_stencil(const OpView& A, const double* __restrict__ m, int64_t c, int i,
-                                                 int j, int k) {
-  const int64_t sxy = (int64_t)A.nx * A.ny;
-  double acc = A.d[c] * m[c];
-  if (!ADV) {
-    if (i > 0) acc = fma(-A.kx[c - 1], m[c - 1], acc);
-    if (i < A.nx - 1) acc = fma(-A.kx[c], m[c + 1], acc);
-    if (j > 0) acc = fma(-A.ky[c - A.nx], m[c - A.nx], acc);
-    if (j < A.ny - 1) acc = fma(-A.ky[c], m[c + A.nx], acc);
-    if (A.ndim == 3) {
-      if (k > 0) acc = fma(-A.kz[c - sxy], m[c - sxy], acc);
-      if (k < A.nz - 1) acc = fma(-A.kz[c], m[c + sxy], acc);
-    }
-    return acc;
-  }
-  if (i > 0) acc = fma(-(A.kx[c - 1] + (A.u0 == -1 ? A.a0 : 0.0)), m[c - 1], acc);
-  if (i < A.nx - 1) acc = fma(-(A.kx[c] + (A.u0 == 1 ? A.a0 : 0.0)), m[c + 1], acc);
-  if (j > 0) acc = fma(-(A.ky[c - A.nx] + (A.u1 == -1 ? A.a1 : 0.0)), m[c - A.nx], acc);
-  if (j < A.ny - 1) acc = fma(-(A.ky[c] + (A.u1 == 1 ? A.a1 : 0.0)), m[c + A.nx], acc);
-  if (A.ndim == 3) {
-    if (k > 0) acc = fma(-(A.kz[c - sxy] + (A.u2 == -1 ? A.a2 : 0.0)), m[c - sxy], acc);
-    if (k < A.nz - 1) acc = fma(-(A.kz[c] + (A.u2 == 1 ? A.a2 : 0.0)), m[c + sxy], acc);
-  }
-  return acc;
-}
 
 __device__ __forceinline__ double op_row_csr(const OpView& A, const double* __restrict__ m, int64_t r) {
   double acc = 0.0;
@@ -136,12 +99,11 @@ __device__ __forceinline__ double op_row_csr(const OpView& A, const double* __re
   return acc;
 }
 
-// Warps walk "chunks" of 32 consecutive unknowns: for a stencil, 32 cells of
-// one x-row (the row gives j, k); for CSR, 32 consecutive rows.  Each chunk's
-// w values and stored s_k values are staged in shared memory and lane jj of
-// the warp sums w_e s_{k_jj,e} over the chunk (the same transposed window dot
-// as in the PIPEFCG pass).
-template <int NW, bool STENCIL, bool ADV = false>
+// CSR operators: warps walk "chunks" of 32 consecutive rows.  Each chunk's w
+// values and stored s_k values are staged in shared memory and lane jj of the
+// warp sums w_e s_{k_jj,e} over the chunk (the same transposed window dot as
+// in the PIPEFCG pass).
+template <int NW>
 __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_dots(GcrArgs a, OpView A) {
   SolveCtl* ctl = a.ctl;
   if (ctl->status != kRun) return;
@@ -167,8 +129,7 @@ __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_do
   const double* lane_row = s_sk + lane * kGcrStride + warp * 32;
   double g0 = 0.0, g1 = 0.0, g2 = 0.0, gw = 0.0;
 
-  const int64_t cpr = STENCIL ? (A.nx + 31) / 32 : 1;                  // chunks per x-row
-  const int64_t nchunks = STENCIL ? cpr * A.ny * A.nz : (N + 31) / 32;
+  const int64_t nchunks = (N + 31) / 32;
   const int64_t gwarps = (int64_t)gridDim.x * NWARPS;
   for (int64_t ch0 = (int64_t)blockIdx.x * NWARPS; ch0 < nchunks; ch0 += gwarps) {
     // all warps of the block iterate together (block-uniform trip count)
@@ -177,21 +138,10 @@ __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_do
     bool valid = false;
     int64_t c = 0;
     if (ch < nchunks) {
-      if (STENCIL) {
-        const int64_t row = ch / cpr;
-        const int ix = (int)(ch - row * cpr) * 32 + lane;
-        if (ix < A.nx) {
-          valid = true;
-          c = row * A.nx + ix;
-          const int irow = (int)row;
-          wv = op_row_stencil<ADV>(A, a.u, c, ix, irow % A.ny, irow / A.ny);
-        }
-      } else {
-        c = ch * 32 + lane;
-        if (c < N) {
-          valid = true;
-          wv = op_row_csr(A, a.u, c);
-        }
+      c = ch * 32 + lane;
+      if (c < N) {
+        valid = true;
+        wv = op_row_csr(A, a.u, c);
       }
     }
     if (valid) {
@@ -247,8 +197,8 @@ __global__ void __launch_bounds__(kGcrThreads, kGcrBlocksPerSm) pipegcr_apply_do
     // writes w and t.  FP64: 3 nu_{i-1} + 3 + 7 (stencil) + nu_i + 3 FMAs, 1 sub.
     const int nwp = ctl->nw;
     ctl->passes += 1;
-    ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + (STENCIL ? 4 : 0) + nu + 2));
-    ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + (STENCIL ? 7 : 0) + nu + 3) + 1.0);
+    ctl->alg_bytes += 8.0 * (double)N * (double)((5 + 3 * nwp + 6) + (2 + nu + 2));
+    ctl->alg_flops += (double)N * (2.0 * (3 * nwp + 3 + nu + 3) + 1.0);
   }
   static_assert(NWARPS * ND >= 2 * NW + 1, "scalar-phase scratch fits in s_red");
   cgcr_iteration_scalars_block(ctl, i, nu, s_sum[0], s_sum[1], s_sum[2], s_sum + 3, s_red, NW);
@@ -401,16 +351,12 @@ class PipeGcr : public Method {
     a.N = N_; a.mmax = mmax_; a.ctl = env.ctl; a.partials = env.partials;
     const pfk_operator* op = env.op;
     OpView A;
-    A.d = op->d; A.kx = op->kx; A.ky = op->ky; A.kz = op->kz;
-    A.nx = op->nx; A.ny = op->ny; A.nz = op->nz; A.ndim = op->ndim;
-    A.a0 = op->adv[0]; A.a1 = op->adv[1]; A.a2 = op->adv[2];
-    A.u0 = op->upw[0]; A.u1 = op->upw[1]; A.u2 = op->upw[2];
     A.rowptr = op->rowptr; A.colidx = op->colidx; A.vals = op->vals;
     const bool stencil = op->rowptr == nullptr;
     const bool adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
     const int tmpl = gcr_template(mmax_);
     const int ablocks = stream_blocks(env.ctx, N_, 4);
-    const int64_t chunks = stencil ? (int64_t)((op->nx + 31) / 32) * op->ny * op->nz : (N_ + 31) / 32;
+    const int64_t chunks = (N_ + 31) / 32;
     const int64_t need = (chunks + kGcrThreads / 32 - 1) / (kGcrThreads / 32);
     const int64_t cap = (int64_t)env.ctx->num_sms * kGcrBlocksPerSm;
     const int dblocks = (int)(need < cap ? need : cap);
@@ -448,21 +394,15 @@ class PipeGcr : public Method {
     switch (tmpl) {
       case 8:
         pipegcr_advance<8><<<ablocks, kThreads, 0, env.st>>>(a);
-        if (stencil && adv) pipegcr_apply_dots<8, true, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
-        else if (stencil) pipegcr_apply_dots<8, true, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
-        else pipegcr_apply_dots<8, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        pipegcr_apply_dots<8><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         break;
       case 16:
         pipegcr_advance<16><<<ablocks, kThreads, 0, env.st>>>(a);
-        if (stencil && adv) pipegcr_apply_dots<16, true, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
-        else if (stencil) pipegcr_apply_dots<16, true, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
-        else pipegcr_apply_dots<16, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        pipegcr_apply_dots<16><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         break;
       default:
         pipegcr_advance<32><<<ablocks, kThreads, 0, env.st>>>(a);
-        if (stencil && adv) pipegcr_apply_dots<32, true, true><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
-        else if (stencil) pipegcr_apply_dots<32, true, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
-        else pipegcr_apply_dots<32, false><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
+        pipegcr_apply_dots<32><<<dblocks, kGcrThreads, 0, env.st>>>(a, A);
         break;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
