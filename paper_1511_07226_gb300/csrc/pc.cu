@@ -133,20 +133,44 @@ __global__ void __launch_bounds__(kThreads) noisy_row_norms_kernel(const double*
 // Inner Jacobi-PCG
 // ---------------------------------------------------------------------------
 
-// A_i.  i = 0: r_0 = v.  i >= 1: r_i = r_{i-1} - alpha_{i-1} s_{i-1}.
-// Finalize: gamma_0, or beta_i = gamma_i / gamma_{i-1} (stop if gamma_i == 0).
+// A_0 and B_0 in one launch (neither needs the other's result):
+// r_0 = v (not stored: A_1 reads v), p_0 = D^-1 r_0, gamma_0 = <D^-1 r_0, r_0>;
+// finalize: stop at once (B(v) = 0) if gamma_0 == 0 (then v and p_0 are zero).
+template <typename V, typename C>
+__global__ void __launch_bounds__(kThreads) pcg_first_kernel(StencilT<V, C> A, const double* __restrict__ v,
+                                                             V* __restrict__ p0, PcCtl* ctl, int k,
+                                                             double* partials, const int* __restrict__ status) {
+  SKIP_IF_DONE(status);
+  V accv = V(0);
+  GRID_LOOP(c, A.n) {
+    const V rv = (V)v[c];
+    const V z = cv<V, C>(A.dinv[c]) * rv;
+    p0[c] = z;
+    accv += z * rv;
+  }
+  double acc[1] = {(double)accv};
+  __shared__ double smem[kThreads / 32];
+  __shared__ double sums[1];
+  if (reduce_last_block<1>(acc, 1, partials, 1, &ctl->counter, smem, sums) && threadIdx.x == 0) {
+    const double g = sums[0];
+    ctl->gamma = g;
+    ctl->ok = (g == 0.0) ? 0 : k;
+  }
+}
+
+// A_i (i >= 1).  r_i = r_{i-1} - alpha_{i-1} s_{i-1} (r_0 = v).
+// Finalize: beta_i = gamma_i / gamma_{i-1} (stop if gamma_i == 0).
 template <typename V, typename C>
 __global__ void __launch_bounds__(kThreads) pcg_a_kernel(StencilT<V, C> A, const double* __restrict__ v,
                                                          V* __restrict__ r, const V* __restrict__ s, PcCtl* ctl,
-                                                         int i, int k, double* partials,
-                                                         const int* __restrict__ status) {
+                                                         int i, double* partials, const int* __restrict__ status) {
   SKIP_IF_DONE(status);
   const int last_x = ctl->ok;
-  if (i >= 1 && i > last_x) return;
-  const V alpha = i >= 1 ? (V)ctl->alpha[i - 1] : V(0);
+  if (i > last_x) return;
+  const V alpha = (V)ctl->alpha[i - 1];
   V accv = V(0);
   GRID_LOOP(c, A.n) {
-    V rv = (i == 0) ? (V)v[c] : r[c] - alpha * s[c];
+    const V rv = (i == 1 ? (V)v[c] : r[c]) - alpha * s[c];
     r[c] = rv;
     accv += (cv<V, C>(A.dinv[c]) * rv) * rv;
   }
@@ -155,10 +179,7 @@ __global__ void __launch_bounds__(kThreads) pcg_a_kernel(StencilT<V, C> A, const
   __shared__ double sums[1];
   if (reduce_last_block<1>(acc, 1, partials, 1, &ctl->counter, smem, sums) && threadIdx.x == 0) {
     const double g = sums[0];
-    if (i == 0) {
-      ctl->gamma = g;
-      ctl->ok = (g == 0.0) ? 0 : k;
-    } else if (g == 0.0) {
+    if (g == 0.0) {
       ctl->ok = i;
     } else {
       ctl->beta[i] = g / ctl->gamma;
@@ -167,8 +188,8 @@ __global__ void __launch_bounds__(kThreads) pcg_a_kernel(StencilT<V, C> A, const
   }
 }
 
-// B_i.  x_i = x_{i-1} + alpha_{i-1} p_{i-1} (i >= 1, while i <= last_x);
-//       p_i = D^-1 r_i + beta_i p_{i-1} (p_0 = D^-1 r_0), while i < last_x.
+// B_i (i >= 1).  x_i = x_{i-1} + alpha_{i-1} p_{i-1} (while i <= last_x);
+//                p_i = D^-1 r_i + beta_i p_{i-1} (while i < last_x).
 template <typename V, typename C>
 __global__ void __launch_bounds__(kThreads) pcg_b_kernel(StencilT<V, C> A, const V* __restrict__ r,
                                                          const V* __restrict__ pold, V* __restrict__ pnew,
@@ -176,14 +197,13 @@ __global__ void __launch_bounds__(kThreads) pcg_b_kernel(StencilT<V, C> A, const
                                                          const int* __restrict__ status) {
   SKIP_IF_DONE(status);
   const int last_x = ctl->ok;
-  const bool do_x = i >= 1 && i <= last_x;
+  if (i > last_x) return;                  // x_i is not formed (and neither is p_i)
   const bool do_p = i < last_x;
-  if (!do_x && !do_p) return;
-  const V alpha = i >= 1 ? (V)ctl->alpha[i - 1] : V(0);
-  const V beta = i >= 1 ? (V)ctl->beta[i] : V(0);
+  const V alpha = (V)ctl->alpha[i - 1];
+  const V beta = (V)ctl->beta[i];
   GRID_LOOP(c, A.n) {
-    V po = i >= 1 ? pold[c] : V(0);
-    if (do_x) x[c] = (i == 1 ? V(0) : x[c]) + alpha * po;
+    const V po = pold[c];
+    x[c] = (i == 1 ? V(0) : x[c]) + alpha * po;
     if (do_p) pnew[c] = cv<V, C>(A.dinv[c]) * r[c] + beta * po;
   }
 }
@@ -443,8 +463,7 @@ static cudaError_t inner_pcg(const pfk_pc* pc, StencilT<V, C> A, const double* v
   const int units = tiled_stencil_setup<V, C>(T, op, A.d, A.kx, A.ky, A.kz, slots);
   const int tblocks = units < pc->partials_cap ? units : pc->partials_cap;
   PcCtl* ctl = pc->ctl;
-  pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, 0, k, pc->partials, status);
-  pcg_b_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, r, nullptr, p[0], x, ctl, 0, status);
+  pcg_first_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, p[0], ctl, k, pc->partials, status);
   // reduced precision on an aligned 3-D grid: the TMA-pipelined walk
   bool tma = false;
   TmaMaps maps[2];
@@ -472,7 +491,7 @@ static cudaError_t inner_pcg(const pfk_pc* pc, StencilT<V, C> A, const double* v
   };
   pcg_c(p[0], 0);
   for (int i = 1; i < k; ++i) {
-    pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, i, k, pc->partials, status);
+    pcg_a_kernel<V, C><<<blocks, kThreads, 0, st>>>(A, v, r, s, ctl, i, pc->partials, status);
     pcg_b_kernel<V, C><<<sblocks, kThreads, 0, st>>>(A, r, p[(i - 1) & 1], p[i & 1], x, ctl, i, status);
     pcg_c(p[i & 1], i);
   }
