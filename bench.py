@@ -41,7 +41,7 @@ UNIT = "solves/s"
 WORKLOAD = "PIPEFCG nu_max=30, 3D 128^3 variable-coefficient Poisson (contrast 1e6), 4 inner Jacobi-PCG (FP64), rtol 1e-8"
 
 # FP64 FMA peak of GB300: 2 FP64 FMA per clock per SM x 152 SMs x 2 flops x
-# 2.07 GHz maximum SM clock = 1.259 TFLOP/s (the recipe's 1.25 TFLOP/s; a
+# 2.07 GHz maximum SM clock = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s; a
 # dependent-FMA probe measured 1.19).  The fused pass does ~1.2 FP64 FMA per
 # 8-byte word it moves, above the HBM balance point of ~0.4, so it is bound by
 # this FP64 pipe, not by HBM.
@@ -415,7 +415,7 @@ def main():
         "roofline": {"kernel": "pipefcg_pass<32> (fused MAXPY + advance + multi-dot)", "bound": "alu",
                      "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic, "traffic_note": traffic_note,
-                     "peak_source": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (recipe's 1.25 TFLOP/s)",
+                     "peak_source": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": achieved_gbs / hbm_peak, "avg_pass_ms": pass_ms,
                      "alg_bytes_per_pass": pass_bytes, "alg_flops_per_pass": pass_flops,
