@@ -64,3 +64,13 @@ def test_fgmres(ctx, m, pc_kind):
     aop = O.StencilOperator(c["dims"], c["eta"], (5.0, 0.0, 0.0))
     mk = (lambda: PC.JacobiPC(aop)) if pc_kind == "jacobi" else (lambda: PC.InnerPCG(aop, 4))
     _run(ctx, "fgmres", c, aop, mk, pc_kind, vel=(5.0, 0.0, 0.0), mmax=m, rtol=1e-8, maxit=800)
+
+
+def test_fgmres_nonsymmetric_csr(ctx):
+    """FGMRES on an assembled (CSR) advection operator: the row-per-thread
+    operator path of the base methods."""
+    vel = (10.0, -5.0, 2.0)
+    c = W.poisson3d_gaussian(dims=(18, 16, 12), ell=4.0, log_contrast=1.5, config_id=2, item_id=9)
+    aop = O.StencilOperator(c["dims"], c["eta"], vel).to_csr()
+    _run(ctx, "fgmres", c, aop, lambda: PC.JacobiPC(aop), "jacobi", storage="csr", vel=vel, mmax=20,
+         rtol=1e-8, maxit=800)
