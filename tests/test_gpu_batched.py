@@ -80,3 +80,24 @@ def test_batched_fp32_preconditioner(ctx):
         assert info["rnorm_true"] <= 1e-8 * info["bnorm"]
         aop = O.StencilOperator(c["dims"], c["eta"])
         assert np.linalg.norm(c["b"] - aop.apply(x)) <= 1e-8 * np.linalg.norm(c["b"]) * (1 + 1e-6)
+
+
+def test_batched_advection_first_iterations(ctx):
+    """Operators with an upwind advection part (2D and 3D) in one batch: the
+    first iterations of each system against the oracle (strict)."""
+    from paper_1511_07226_gb300 import pfk
+    # mild contrast and advection: no norm breakdown within the compared iterations
+    cases = [(W.batched2d_system(j, s, log_contrast=0.25, config_id=4), vel) for j, (s, vel) in
+             enumerate([(37, (3.0, -2.0, 0.0)), (52, (-4.0, 1.0, 0.0))])]
+    c3 = W.poisson3d_gaussian(dims=(12, 10, 9), ell=3.0, log_contrast=1.0, config_id=4, item_id=90)
+    cases.append((c3, (0.2, 0.1, -0.3)))
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"], vel) for c, vel in cases]
+    xs, infos, hists = pfk.solve_batched(ctx, ops, [c["b"] for c, _ in cases], pc_kind="jacobi", history=32,
+                                         block_threads=256, mmax=20, rtol=1e-8, maxit=12)
+    for (c, vel), h in zip(cases, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"], vel)
+        ref = K.solve("pipefcg", aop, PC.JacobiPC(aop), c["b"], prm=K.Params(mmax=20, rtol=1e-8, maxit=12))
+        rho = ref.rho()
+        assert ref.breakdowns == 0
+        assert len(h) == len(rho)
+        assert np.allclose(h[:, 0], rho, rtol=1e-10, atol=0.0), c["dims"]
