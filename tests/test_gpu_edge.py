@@ -1,8 +1,8 @@
 """Edge and degenerate cases of the solve path on the GPU, each against what
 the method or the oracle fixes: b = 0, one-cell and one-row grids, an exact
 preconditioner (B = A^-1 gives one step with alpha_0 = 1), nu_max = 1 (IPCG,
-Sec. 5 truncation remark), and argument errors that must leave the context
-usable."""
+Sec. 5 truncation remark), the largest window (nu_max = 32), and argument
+errors that must leave the context usable."""
 import numpy as np
 import pytest
 
@@ -84,6 +84,24 @@ def test_nu_max_one_is_ipcg(ctx):
     x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "inner_pcg", 3), c["b"], method="pipefcg",
                               mmax=1, rtol=1e-8, maxit=800, history=2000)
     check_solve(hist, info, ref, alts, rtol=1e-8)
+
+
+@pytest.mark.parametrize("method", ["pipefcg", "pipegcr", "fcg", "pipefgmres", "fgmres"])
+def test_largest_window(ctx, method):
+    """nu_max / restart length at its maximum (PFK_MAX_MMAX = 32): a full window
+    occupies every lane of the transposed window dots and the widest
+    reductions; against the oracle."""
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(dims=(18, 16, 13), ell=3.0, log_contrast=2.0, config_id=2, item_id=34)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    sigma = {"sigma": 1.5} if "gmres" in method else {}
+    prm = K.Params(mmax=32, rtol=1e-9, maxit=600, **sigma)
+    ref, alts = oracle_with_envelope(method, aop, lambda: PC.JacobiPC(aop), c["b"], prm)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], method=method, mmax=32,
+                              rtol=1e-9, maxit=600, history=4000, **sigma)
+    assert ref.iterations > 40                  # the window fills and slides
+    check_solve(hist, info, ref, alts, rtol=1e-9)
 
 
 def test_errors_leave_context_usable(ctx):
