@@ -1,8 +1,8 @@
 """Edge and degenerate cases of the solve path on the GPU, each against what
 the method or the oracle fixes: b = 0, one-cell and one-row grids, an exact
 preconditioner (B = A^-1 gives one step with alpha_0 = 1), nu_max = 1 (IPCG,
-Sec. 5 truncation remark), the largest window (nu_max = 32), and argument
-errors that must leave the context usable."""
+Sec. 5 truncation remark), the largest window (nu_max = 32), a nonzero
+initial guess, and argument errors that must leave the context usable."""
 import numpy as np
 import pytest
 
@@ -102,6 +102,23 @@ def test_largest_window(ctx, method):
                               rtol=1e-9, maxit=600, history=4000, **sigma)
     assert ref.iterations > 40                  # the window fills and slides
     check_solve(hist, info, ref, alts, rtol=1e-9)
+
+
+@pytest.mark.parametrize("method", ALL)
+def test_nonzero_initial_guess(ctx, method):
+    """x_0 != 0 for every method (r_0 = b - A x_0; FGMRES types update x_0 +
+    U y at the cycle end), against the oracle from the same x_0."""
+    from paper_1511_07226_gb300 import pfk
+    c = W.poisson3d_gaussian(dims=(15, 13, 11), ell=3.0, log_contrast=1.5, config_id=2, item_id=35)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    x0 = W.random_vector(aop.n, 36)
+    sigma = {"sigma": 1.5} if "gmres" in method else {}
+    prm = K.Params(mmax=20, rtol=1e-8, maxit=600, **sigma)
+    ref, alts = oracle_with_envelope(method, aop, lambda: PC.JacobiPC(aop), c["b"], prm, x0=x0)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], x0=x0, method=method,
+                              mmax=20, rtol=1e-8, maxit=600, history=4000, **sigma)
+    check_solve(hist, info, ref, alts, rtol=1e-8)
 
 
 def test_errors_leave_context_usable(ctx):
