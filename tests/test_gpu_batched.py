@@ -101,3 +101,18 @@ def test_batched_advection_first_iterations(ctx):
         assert ref.breakdowns == 0
         assert len(h) == len(rho)
         assert np.allclose(h[:, 0], rho, rtol=1e-10, atol=0.0), c["dims"]
+
+
+def test_batched_nonzero_initial_guess(ctx):
+    """x_0 != 0 per system (r_0 = b - A x_0 in the fill), against the oracle."""
+    from paper_1511_07226_gb300 import pfk
+    sys_ = _systems([30, 45])
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys_]
+    x0s = [W.random_vector(int(np.prod(c["dims"])), 40 + j) for j, c in enumerate(sys_)]
+    xs, infos, hists = pfk.solve_batched(ctx, ops, [c["b"] for c in sys_], x0s=x0s, pc_kind="jacobi", history=2000,
+                                         block_threads=256, mmax=20, rtol=1e-8, maxit=1000)
+    for c, x0, info, h in zip(sys_, x0s, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.JacobiPC(aop), c["b"],
+                                         K.Params(mmax=20, rtol=1e-8, maxit=1000), x0=x0)
+        check_solve(h, info, ref, alts, rtol=1e-8)
