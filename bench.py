@@ -247,6 +247,8 @@ def main():
     ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase", "batched"],
                     help="--ncu-case problem: Gaussian-field Poisson (4 inner PCG), two-phase advection "
                          "(8 Chebyshev sweeps), or the first --n systems of the batched workload")
+    ap.add_argument("--block-threads", type=int, default=256,
+                    help="threads per block of the --case batched profiler case")
     ap.add_argument("--extras", default="fcg,pipegcr,nu_sweep,stokes,batched,fgmres256,serve",
                     help="comma-separated secondary measurements (fcg, pipegcr, nu_sweep, stokes, batched, "
                          "fgmres256, serve; serve_sweep is opt-in) or 'none'")
@@ -262,7 +264,7 @@ def main():
         ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys_]
         _, infos, _ = pfk.solve_batched(ctx, ops, [c["b"] for c in sys_], pc_kind="inner_pcg", inner_iters=4,
                                         precision="fp32", mmax=20, rtol=1e-8, maxit=args.maxit,
-                                        block_threads=256)
+                                        block_threads=args.block_threads)
         print(json.dumps({"ncu_case": "batched", "systems": len(ops),
                           "iterations": int(sum(i["iterations"] for i in infos))}))
         return
