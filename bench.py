@@ -587,13 +587,14 @@ def extra_fgmres256(ctx, dev, args) -> dict:
     return out
 
 
-def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0) -> dict:
-    """Replays requests through a fresh server at their arrival times scaled by
-    rate_scale (2 = twice as far apart); returns latency and throughput."""
+def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo") -> dict:
+    """Replays requests through a fresh server (admission `order`) at their
+    arrival times scaled by rate_scale (2 = twice as far apart); returns latency
+    and throughput."""
     import workloads as W
     from paper_1511_07226_gb300 import pfk
     meth = {0: "pipefcg", 1: "pipegcr", 2: "pipefgmres"}
-    srv = pfk.Server(ctx, workers=workers)
+    srv = pfk.Server(ctx, workers=workers, order=order)
     kw = dict(mmax=30, rtol=1e-8, maxit=20000, max_restarts=MAX_RESTARTS)
     # warm-up: one small request per method (graphs, module loading)
     for m in meth.values():
@@ -611,7 +612,7 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0) -> dict:
     srv.close()
     lat = np.array([res[2] for res in results])
     unknowns = int(sum(r["side"] ** 3 for r in reqs))
-    return {"workers": workers, "requests": len(reqs),
+    return {"workers": workers, "order": order, "requests": len(reqs),
             "converged": int(sum(res[1]["status_name"] == "ok" for res in results)),
             "offered_rate_per_s": len(reqs) / max(rate_scale * (reqs[-1]["t"] - reqs[0]["t"]), 1e-9),
             "solves_per_s": len(reqs) / wall, "unknowns_per_s": unknowns / wall,
@@ -629,6 +630,8 @@ def extra_serve(ctx, dev, args) -> dict:
     probs = [W.request_problem(r) for r in reqs]
     out = _serve_replay(ctx, reqs, probs, args.serve_workers)
     out["workload"] = f"first {len(reqs)} requests of the seeded stream, replayed at their arrival times"
+    # the same replay with the smallest queued request admitted first
+    out["smallest_first"] = _serve_replay(ctx, reqs, probs, args.serve_workers, order="smallest_first")
     return out
 
 

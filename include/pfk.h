@@ -360,7 +360,8 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
 /* ------------------------------------------------------------------------ */
 
 /* A server accepts solve requests at any time, queues them in arrival order
- * and admits the head of the queue as soon as a worker is free and the device
+ * and admits the next one (by pfk_server_params.order: the head of the queue,
+ * or the smallest queued request) as soon as a worker is free and the device
  * memory the active solves hold (operator, preconditioner scratch, Krylov
  * workspace) plus the new request's estimate fits the budget; a request larger
  * than the budget still runs when nothing else is active.  Each worker owns a
@@ -372,10 +373,18 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
  * thread may submit and poll). */
 typedef struct pfk_server pfk_server;
 
+/* Admission order of queued requests (a scheduling choice; the paper has no
+ * counterpart).  FIFO: arrival order.  SMALLEST_FIRST: the queued request with
+ * the fewest unknowns (earliest arrival among equals) -- a lower median
+ * latency for an oversubscribed stream, large requests wait longer. */
+typedef enum { PFK_SERVE_FIFO = 0, PFK_SERVE_SMALLEST_FIRST = 1 } pfk_serve_order;
+
 typedef struct {
   int32_t workers;         /* concurrent solves; 0 = 4 */
   int32_t queue_capacity;  /* queued + active requests; 0 = 4096 */
   int64_t memory_budget;   /* device bytes for active solves; 0 = 80 % of free memory */
+  int32_t order;           /* pfk_serve_order; 0 = FIFO */
+  int32_t reserved;        /* 0 */
 } pfk_server_params;
 
 typedef struct {

@@ -1,8 +1,10 @@
 // Serving loop: continuous batching of independent solves (host runtime).
 //
 // Requests are copied at submission and queued in arrival order.  Worker
-// threads, each with its own CUDA stream and pfk_context, admit the head of the
-// queue when the device-memory budget allows (memory of the active solves is
+// threads, each with its own CUDA stream and pfk_context, admit the next
+// request (the head of the queue, or with PFK_SERVE_SMALLEST_FIRST the queued
+// request with the fewest unknowns) when the device-memory budget allows
+// (memory of the active solves is
 // accounted from each request's estimate), run the whole solve through the
 // graph-replayed single-system path, publish the result and release the
 // memory.  Kernels of the active solves run concurrently on the GPU; a request
@@ -57,6 +59,7 @@ struct pfk_server {
   int64_t in_use = 0;
   int active = 0;
   int capacity = 0;
+  int order = PFK_SERVE_FIFO;
   bool stop = false;
   uint64_t next_ticket = 1;
   std::deque<std::shared_ptr<Item>> queue;
@@ -92,6 +95,15 @@ int64_t estimate_bytes(const Item& it, int num_sms) {
   return op + pc + ws + partials + 2 * n * 8;
 }
 
+// The request admitted next (the queue is not empty; srv->mu held).
+std::deque<std::shared_ptr<Item>>::iterator next_request(pfk_server* srv) {
+  auto best = srv->queue.begin();
+  if (srv->order == PFK_SERVE_SMALLEST_FIRST)
+    for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
+      if ((*q)->n < (*best)->n) best = q;
+  return best;
+}
+
 void worker_main(pfk_server* srv, int index) {
   cudaSetDevice(srv->device);
   pfk_context* ctx = srv->ctxs[index];
@@ -102,12 +114,13 @@ void worker_main(pfk_server* srv, int index) {
       srv->cv_work.wait(lk, [&] {
         if (srv->stop) return true;
         if (srv->queue.empty()) return false;
-        const auto& head = srv->queue.front();
-        return srv->active == 0 || srv->in_use + head->bytes <= srv->budget;
+        const auto& next = *next_request(srv);
+        return srv->active == 0 || srv->in_use + next->bytes <= srv->budget;
       });
       if (srv->stop) break;
-      it = srv->queue.front();
-      srv->queue.pop_front();
+      const auto pos = next_request(srv);
+      it = *pos;
+      srv->queue.erase(pos);
       srv->in_use += it->bytes;
       srv->active += 1;
     }
@@ -175,6 +188,12 @@ pfk_status pfk_server_create(pfk_context* ctx, const pfk_server_params* params, 
   srv->device = ctx->device;
   const int workers = params && params->workers > 0 ? params->workers : 4;
   srv->capacity = params && params->queue_capacity > 0 ? params->queue_capacity : 4096;
+  if (params && params->order != PFK_SERVE_FIFO && params->order != PFK_SERVE_SMALLEST_FIRST) {
+    delete srv;
+    set_error(ctx, "unknown admission order");
+    return PFK_ERR_INVALID;
+  }
+  srv->order = params ? params->order : PFK_SERVE_FIFO;
   int64_t budget = params ? params->memory_budget : 0;
   if (budget <= 0) {
     size_t fr = 0, tot = 0;

@@ -58,7 +58,11 @@ class InnerSolve(C.Structure):
 
 
 class ServerParams(C.Structure):
-    _fields_ = [("workers", C.c_int32), ("queue_capacity", C.c_int32), ("memory_budget", C.c_int64)]
+    _fields_ = [("workers", C.c_int32), ("queue_capacity", C.c_int32), ("memory_budget", C.c_int64),
+                ("order", C.c_int32), ("reserved", C.c_int32)]
+
+
+SERVE_ORDERS = {"fifo": 0, "smallest_first": 1}
 
 
 class Request(C.Structure):
@@ -445,10 +449,12 @@ class Server:
     time, poll for results.  Requests carry host arrays, which are copied at
     submission; each result is bitwise that of the same request solved alone."""
 
-    def __init__(self, ctx: Context, workers: int = 4, queue_capacity: int = 0, memory_budget: int = 0):
+    def __init__(self, ctx: Context, workers: int = 4, queue_capacity: int = 0, memory_budget: int = 0,
+                 order: str = "fifo"):
         self.ctx = ctx
         p = ServerParams()
         p.workers, p.queue_capacity, p.memory_budget = int(workers), int(queue_capacity), int(memory_budget)
+        p.order = SERVE_ORDERS[order]
         h = C.c_void_p()
         _check(load().pfk_server_create(ctx.h, C.byref(p), C.byref(h)), ctx.h)
         self.h = h

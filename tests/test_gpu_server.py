@@ -136,3 +136,37 @@ def test_csr_requests_and_validation(ctx):
 def _csr_arrays(c):
     csr = O.StencilOperator(c["dims"], c["eta"]).to_csr()
     return csr.rowptr, csr.colidx, csr.vals
+
+
+def test_smallest_first_order(ctx):
+    """PFK_SERVE_SMALLEST_FIRST with a budget below any request's estimate:
+    one request at a time; the first one admitted starts while the others are
+    still being queued, the rest run by increasing size; every result equals
+    the request solved alone."""
+    from paper_1511_07226_gb300 import pfk
+    reqs = _requests(6, 14, 30)
+    srv = pfk.Server(ctx, workers=4, memory_budget=1, order="smallest_first")
+    t0, tickets = [], []
+    for r, c in reqs:
+        t0.append(time.perf_counter())
+        tickets.append(srv.submit(c["dims"], c["eta"], c["b"], method=METHOD_OF[r["method"]], **KW))
+    results = [srv.poll(t) for t in tickets]
+    srv.close()
+    done = [ts + lat / 1e3 for ts, (_, _, lat) in zip(t0, results)]
+    first = int(np.argmin(done))
+    rest = sorted((j for j in range(len(reqs)) if j != first), key=lambda j: (reqs[j][0]["side"], j))
+    # after the first admitted request (admitted before the others arrived),
+    # completions follow the size order (equal sizes by arrival), up to clock
+    # jitter
+    order = [done[j] for j in rest]
+    assert all(b >= a - 2e-3 for a, b in zip(order, order[1:])), (rest, np.diff(order))
+    for (r, c), (x, info, _) in zip(reqs, results):
+        xa, ia = _alone(ctx, c, METHOD_OF[r["method"]])
+        assert info["status_name"] == ia["status_name"] == "ok"
+        assert np.array_equal(x, xa)
+
+
+def test_unknown_order_rejected(ctx):
+    from paper_1511_07226_gb300 import pfk
+    with pytest.raises(KeyError):
+        pfk.Server(ctx, order="largest_first")
