@@ -411,6 +411,21 @@ pfk_status pfk_poll(pfk_server* srv, uint64_t ticket, double* x_out, pfk_solve_i
 pfk_status pfk_server_destroy(pfk_server* srv);
 
 /* ------------------------------------------------------------------------ */
+/* Measurement                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* FP64 FMA throughput of the device, the denominator of the "alu" roofline of
+ * the FP64 Krylov kernels (none of them is a dense contraction; on GB300 their
+ * FP64 arithmetic, not HBM, bounds them).  The paper has no counterpart: it is
+ * a measurement of the machine.  Runs a kernel of eight independent FMA chains
+ * per thread, 8 blocks of 256 threads per SM, `iters` steps per chain (1 <=
+ * iters <= 2^24), once to warm up and once timed with CUDA events on ctx's
+ * stream.  *tflops = 16 iters threads / time (an FMA counts 2 flops), *ms =
+ * the timed launch.  Returns after the work completes.
+ * Errors: PFK_ERR_INVALID, PFK_ERR_CUDA. */
+pfk_status pfk_probe_fp64_fma(pfk_context* ctx, int iters, double* tflops, double* ms);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free preconditioner application                                */
 /* ------------------------------------------------------------------------ */
 
@@ -436,7 +451,9 @@ pfk_status pfk_server_destroy(pfk_server* srv);
  *    streams, other host threads, other contexts on the same device) race and
  *    give wrong results.  Each call clears the parts that must start at zero.
  *  - Ordered on ctx's stream; returns after the work completes.
- * Errors: PFK_ERR_INVALID, PFK_ERR_CUDA. */
+ * Errors: PFK_ERR_INVALID (also when the reduction grid, up to 8 blocks per
+ * SM, would need more than the scratch's 2048 partial sums: a GPU with more
+ * than 256 SMs), PFK_ERR_CUDA. */
 pfk_status pfk_pc_apply_inner_pcg_noalloc(pfk_context* ctx, const pfk_operator* op, int inner_iters,
                                           const double* v, double* y);
 

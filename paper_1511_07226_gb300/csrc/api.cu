@@ -20,6 +20,7 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
                      const double* b, double* x, pfk_solve_info* info);
 pfk_status solve_workspace_bytes(int method, int mmax, int64_t n, int64_t* bytes);
 bool method_supported(int method);
+cudaError_t fp64_probe(pfk_context* ctx, int iters, double* tflops, double* ms_out);
 
 static thread_local std::string g_thread_error;
 
@@ -358,6 +359,15 @@ pfk_status pfk_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
     if (e != cudaSuccess && s == PFK_OK) return cuda_fail(ctx, e, "copy back");
   }
   return s;
+}
+
+pfk_status pfk_probe_fp64_fma(pfk_context* ctx, int iters, double* tflops, double* ms) {
+  CHECK_ARG(ctx, ctx != nullptr, "NULL context");
+  CHECK_ARG(ctx, tflops != nullptr && ms != nullptr, "NULL output pointer");
+  CHECK_ARG(ctx, iters >= 1 && iters <= (1 << 24), "iters must be in [1, 2^24]");
+  cudaSetDevice(ctx->device);
+  PFK_CUDA(ctx, fp64_probe(ctx, iters, tflops, ms));
+  return PFK_OK;
 }
 
 }  // extern "C"

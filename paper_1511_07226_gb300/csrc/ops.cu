@@ -396,3 +396,56 @@ pfk_status create_csr(pfk_context* ctx, const pfk_operator_desc* desc, pfk_opera
 }
 
 }  // namespace pfk
+
+// ---------------------------------------------------------------------------
+// FP64 FMA-rate probe (measurement of the ALU roofline's denominator)
+// ---------------------------------------------------------------------------
+
+namespace pfk {
+
+// Eight independent FMA chains per thread, `iters` steps each: the FP64 pipe
+// is kept busy by ILP and occupancy alone (no memory traffic).  The multiplier
+// is just below 1 and the addend tiny, so the values stay finite; the store is
+// conditional on an impossible value so the chains are not optimised away.
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters, double m, double c, double* out) {
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = 1.0 + 1e-3 * (double)(threadIdx.x + j);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s == -1.0) out[0] = s;
+}
+
+cudaError_t fp64_probe(pfk_context* ctx, int iters, double* tflops, double* ms_out) {
+  cudaStream_t st = ctx->stream;
+  const int blocks = ctx->num_sms * 8;   // 2048 threads per SM
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  float ms = 0.f;
+  fp64_fma_probe_kernel<<<blocks, 256, 0, st>>>(iters, 0.9999999, 1e-9, ctx->scratch_out);   // warm-up
+  if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(e0, st)) == cudaSuccess) {
+    fp64_fma_probe_kernel<<<blocks, 256, 0, st>>>(iters, 0.9999999, 1e-9, ctx->scratch_out);
+    if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(e1, st)) == cudaSuccess &&
+        (e = cudaEventSynchronize(e1)) == cudaSuccess)
+      e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  const double flops = 2.0 * 8.0 * (double)iters * (double)blocks * 256.0;
+  *ms_out = ms;
+  *tflops = ms > 0.f ? flops / ((double)ms * 1e-3) / 1e12 : 0.0;
+  return cudaSuccess;
+}
+
+}  // namespace pfk

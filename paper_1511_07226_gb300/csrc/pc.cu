@@ -705,7 +705,11 @@ pfk_status create_pc(pfk_context* ctx, const pfk_operator* op, const pfk_pc_desc
 namespace pfk {
 
 constexpr int64_t kNoallocMaxN = PFK_NOALLOC_MAX_N;
-constexpr int64_t kNoallocPartials = 2048;   // >= 2 blocks per SM on any current GPU
+// One partial sum per block of the inner PCG's reduction kernels: pcg_first and
+// pcg_a launch up to 8 blocks per SM (stream_blocks(ctx, n, 8)), never more
+// than one block per 256 unknowns, and the stencil walk is capped at this
+// count; a call whose grid would exceed it is rejected.
+constexpr int64_t kNoallocPartials = 2048;
 constexpr int64_t kNoallocCtlDoubles = (sizeof(PcCtl) + sizeof(double) - 1) / sizeof(double);
 constexpr int64_t kNoallocDoubles = 5 * kNoallocMaxN + kNoallocPartials + kNoallocCtlDoubles;
 
@@ -755,6 +759,11 @@ extern "C" pfk_status pfk_pc_apply_inner_pcg_noalloc(pfk_context* ctx, const pfk
   }
   if (op->n > kNoallocMaxN) {
     set_error(ctx, "operator size exceeds PFK_NOALLOC_MAX_N (262144 unknowns), the capacity of the static "
+                   "scratch of the allocation-free entry point");
+    return PFK_ERR_INVALID;
+  }
+  if (stream_blocks(ctx, op->n, 8) > kNoallocPartials) {
+    set_error(ctx, "the inner PCG's reduction grid on this GPU exceeds the 2048 partial sums of the static "
                    "scratch of the allocation-free entry point");
     return PFK_ERR_INVALID;
   }

@@ -117,6 +117,7 @@ _SIGS = {
     "pfk_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(SolveInfo), C.POINTER(C.c_double),
                            C.c_int]),
     "pfk_server_destroy": (C.c_int, [C.c_void_p]),
+    "pfk_probe_fp64_fma": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 
@@ -388,6 +389,13 @@ def solve(ctx: Context, op: Operator, pc: Preconditioner | None, b, x0=None, his
     if hist is not None:
         hist = hist[:min(info.history_len, history)]
     return x, d, hist
+
+
+def probe_fp64_fma(ctx: Context, iters: int = 1 << 16) -> dict:
+    """Measured FP64 FMA throughput of the device (the ALU roofline's denominator)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(load().pfk_probe_fp64_fma(ctx.h, int(iters), C.byref(tf), C.byref(ms)), ctx.h)
+    return {"tflops": tf.value, "ms": ms.value, "iters": int(iters)}
 
 
 NOALLOC_MAX_N = 262144
