@@ -42,6 +42,7 @@ extern "C" {
 #define PFK_ABI_VERSION 1
 #define PFK_MAX_MMAX 32        /* largest nu_max / restart length m */
 #define PFK_HISTORY_FIELDS 4   /* per iteration: rho, ||r||_2 (recurred), eta, alpha */
+#define PFK_PERSISTENT_MAX_N 16384   /* largest system of the persistent single-launch path */
 
 typedef enum {
   PFK_OK = 0,
@@ -260,7 +261,16 @@ pfk_status pfk_pc_apply(pfk_context* ctx, const pfk_pc* pc, const double* v, dou
  *  profile     1: record CUDA events around the method's fused recurrence
  *              pass in every iteration (the graphs then carry event nodes and
  *              one graph launch is in flight instead of two) and report the
- *              pass's total device time in pfk_solve_info.pass_ms. */
+ *              pass's total device time in pfk_solve_info.pass_ms.
+ *  persistent  small systems (n <= PFK_PERSISTENT_MAX_N, assembled CSR
+ *              operator, Jacobi or no preconditioner, PIPEFCG or FCG): run
+ *              many iterations per cooperative launch, the blocks meeting at
+ *              bounded grid barriers (one per PIPEFCG iteration, three per FCG
+ *              iteration) instead of kernel boundaries.  0 (default): when
+ *              eligible; 1: never; 2: required (PFK_ERR_INVALID when not
+ *              eligible).  A barrier wait that gives up (2 s) ends the solve
+ *              with PFK_ERR_TIMEOUT.
+ *  reserved    0. */
 typedef struct {
   int32_t method;
   int32_t mmax;
@@ -276,6 +286,8 @@ typedef struct {
   double* history;
   int32_t history_capacity;
   int32_t profile;
+  int32_t persistent;
+  int32_t reserved;
 } pfk_solve_params;
 
 typedef struct {

@@ -334,6 +334,10 @@ class Fcg : public Method {
     P_ = tmp_ + N; S_ = P_ + (mmax + 1) * N;
   }
   double* scratch() override { return tmp_; }
+  bool configure(const pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, int64_t N, int mode) override {
+    persistent_ = mode != 1 && persistent_eligible(ctx, op, pc, PFK_FCG, 0, N);
+    return persistent_;
+  }
   cudaError_t fill(const SolveEnv& env, const double* b, double* x) override {
     cudaError_t e;
     if ((e = op_apply(env.op, x, r_, b, nullptr, env.st)) != cudaSuccess) return e;   // r_0 = b - A x_0
@@ -341,6 +345,14 @@ class Fcg : public Method {
     return launch_apply_dots(env, P_, S_, r_, kApplyFcgFill);                          // s_0 = A p_0, gamma_0, eta_0
   }
   cudaError_t iteration(const SolveEnv& env, double* x) override {
+    if (persistent_) {
+      cudaError_t e = env.mark_pass(0);
+      if (e != cudaSuccess) return e;
+      e = launch_persistent(env, false, mmax_, x, r_, u_, nullptr, nullptr, nullptr, nullptr, P_, S_, nullptr,
+                            nullptr, kPersistentIters);
+      if (e != cudaSuccess) return e;
+      return env.mark_pass(1);
+    }
     const int* status = &env.ctl->status;
     const int tmpl = base_template(mmax_);
     cudaError_t e;
@@ -357,6 +369,7 @@ class Fcg : public Method {
  private:
   int64_t N_ = 0;
   int mmax_ = 0;
+  bool persistent_ = false;
   double *r_ = nullptr, *u_ = nullptr, *tmp_ = nullptr, *P_ = nullptr, *S_ = nullptr;
 };
 

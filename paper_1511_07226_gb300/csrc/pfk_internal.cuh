@@ -36,6 +36,7 @@ enum DevStatus : int {
   kFillBreakdown = 4,   // eta_0 <= 0 in a pipeline fill
   kNonFinite = 5,
   kCycleEnd = 6,        // GMRES types: restart length reached
+  kTimeout = 7,         // a bounded grid-barrier wait of a persistent kernel ran out
 };
 
 // Device control block of one solve.
@@ -66,6 +67,10 @@ struct SolveCtl {
   double alg_flops;        // their FP64 flops (FMA = 2)
   double theta;            // projection coefficient <r_i, w_i>/<r_i, r_i> (eq. proj variant)
   double pend[3];          // reduction results handed from one kernel to the next (PIPEGCR apply)
+  unsigned int bar_count;  // grid barrier of the persistent kernels: arrivals,
+  unsigned int bar_gen;    // generation (bumped by the last arrival),
+  unsigned int bar_abort;  // set when a wait timed out (every block then leaves)
+  unsigned int bar_pad;
 };
 
 // Control block of a preconditioner application (inner iterations).

@@ -289,6 +289,11 @@ class PipeFcg : public Method {
 
   double* scratch() override { return tmp_; }
 
+  bool configure(const pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, int64_t N, int mode) override {
+    persistent_ = mode != 1 && persistent_eligible(ctx, op, pc, PFK_PIPEFCG, naive_ || gcrw_ || theta_, N);
+    return persistent_;
+  }
+
   cudaError_t fill(const SolveEnv& env, const double* b, double* x) override {
     cudaStream_t st = env.st;
     cudaError_t e;
@@ -304,6 +309,14 @@ class PipeFcg : public Method {
   }
 
   cudaError_t iteration(const SolveEnv& env, double* x) override {
+    if (persistent_) {
+      // m alternates between m_ (even iterations, written by the fill) and t_
+      cudaError_t e = env.mark_pass(0);
+      if (e != cudaSuccess) return e;
+      e = launch_persistent(env, true, mmax_, x, r_, u_, w_, m_, t_, n_, P_, S_, Q_, Z_, kPersistentIters);
+      if (e != cudaSuccess) return e;
+      return env.mark_pass(1);
+    }
     FcgArgs a;
     a.x = x; a.r = r_; a.u = u_; a.w = w_; a.m = m_; a.n = n_; a.t = t_;
     a.P = P_; a.S = S_; a.Q = Q_; a.Z = Z_;
@@ -337,6 +350,7 @@ class PipeFcg : public Method {
   bool naive_;
   bool gcrw_;
   bool theta_;
+  bool persistent_ = false;
   int64_t N_ = 0;
   int mmax_ = 0;
   double *r_ = nullptr, *u_ = nullptr, *w_ = nullptr, *m_ = nullptr, *n_ = nullptr, *t_ = nullptr,

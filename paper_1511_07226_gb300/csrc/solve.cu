@@ -144,6 +144,15 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
     set_error(ctx, "method not available");
     return PFK_ERR_INVALID;
   }
+  if (prm->persistent < 0 || prm->persistent > 2) {
+    set_error(ctx, "persistent must be 0 (auto), 1 (never) or 2 (required)");
+    return PFK_ERR_INVALID;
+  }
+  if (!M->configure(ctx, op, pc, N, prm->persistent) && prm->persistent == 2) {
+    set_error(ctx, "the persistent path needs PIPEFCG or FCG, an assembled CSR operator, Jacobi or no "
+                   "preconditioner and n <= PFK_PERSISTENT_MAX_N");
+    return PFK_ERR_INVALID;
+  }
   // ---- workspace: control block | method vectors | partials | scalars | history ----
   // partials: room for any kernel of the solve (at most kMaxBlocksPerSm blocks
   // per SM, at most kPartialStride values per block); launches check it.
@@ -379,6 +388,11 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
     if (status == kNonFinite) {
       set_error(ctx, "non-finite residual norm");
       result = PFK_ERR_BREAKDOWN;
+      break;
+    }
+    if (status == kTimeout) {
+      set_error(ctx, "a grid-barrier wait of the persistent kernel timed out");
+      result = PFK_ERR_TIMEOUT;
       break;
     }
     if (status == kMaxit) {

@@ -49,6 +49,13 @@ class Method {
   virtual cudaError_t end_cycle(const SolveEnv& env, double* x) { (void)env; (void)x; return cudaSuccess; }
   // Number of ring/Hessenberg columns (GMRES types restart after this many).
   virtual int cycle_length() const { return 0; }
+  // Once per solve, before bind: picks the persistent single-launch form when
+  // the method has one, the problem is eligible and `mode` allows it (0 auto,
+  // 1 never, 2 required).  Returns whether it did.
+  virtual bool configure(const pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, int64_t N, int mode) {
+    (void)ctx; (void)op; (void)pc; (void)N; (void)mode;
+    return false;
+  }
   // Once per solve, before the graphs are captured (e.g. the PIPEFGMRES shift
   // estimate); may synchronise.  `dscalar` is a device scalar slot; the method
   // reports the shift it uses (NaN if none) in *host_sigma.
@@ -58,6 +65,16 @@ class Method {
     return cudaSuccess;
   }
 };
+
+// Persistent single-launch iterations (persistent.cu): eligibility, and one
+// cooperative launch of up to `iters` PIPEFCG (pipelined) or FCG iterations.
+// FCG passes w, m0, m1, n, Q, Z as null.
+constexpr int kPersistentIters = 16;
+bool persistent_eligible(const pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, int method, int naive_like,
+                         int64_t N);
+cudaError_t launch_persistent(const SolveEnv& env, bool pipelined, int mmax, double* x, double* r, double* u,
+                              double* w, double* m0, double* m1, double* n, double* P, double* S, double* Q,
+                              double* Z, int iters);
 
 Method* make_pipefcg(bool naive);
 Method* make_pipegcr_w();

@@ -49,7 +49,8 @@ class SolveParams(C.Structure):
     _fields_ = [("method", C.c_int32), ("mmax", C.c_int32), ("truncation", C.c_int32), ("norm", C.c_int32),
                 ("rtol", C.c_double), ("atol", C.c_double), ("maxit", C.c_int32), ("max_restarts", C.c_int32),
                 ("sigma", C.c_double), ("true_residual_check", C.c_int32), ("graph_iters", C.c_int32),
-                ("history", C.c_void_p), ("history_capacity", C.c_int32), ("profile", C.c_int32)]
+                ("history", C.c_void_p), ("history_capacity", C.c_int32), ("profile", C.c_int32),
+                ("persistent", C.c_int32), ("reserved", C.c_int32)]
 
 
 class InnerSolve(C.Structure):
@@ -63,6 +64,7 @@ class ServerParams(C.Structure):
 
 
 SERVE_ORDERS = {"fifo": 0, "smallest_first": 1}
+PERSISTENT = {"auto": 0, "off": 1, "on": 2}
 
 
 class Request(C.Structure):
@@ -340,7 +342,7 @@ def default_params() -> SolveParams:
 
 def make_params(method="pipefcg", mmax=30, truncation="standard", norm="natural", rtol=1e-8, atol=0.0,
                 maxit=10000, max_restarts=20, sigma=float("nan"), true_residual_check=True,
-                graph_iters=8, profile=False) -> SolveParams:
+                graph_iters=8, profile=False, persistent="auto") -> SolveParams:
     p = default_params()
     p.method = METHODS[method]
     p.mmax = int(mmax)
@@ -352,6 +354,7 @@ def make_params(method="pipefcg", mmax=30, truncation="standard", norm="natural"
     p.true_residual_check = 1 if true_residual_check else 0
     p.graph_iters = int(graph_iters)
     p.profile = 1 if profile else 0
+    p.persistent = PERSISTENT[persistent]
     return p
 
 

@@ -83,8 +83,13 @@ def envelope(ref, alts) -> np.ndarray:
     return np.maximum.accumulate(env)
 
 
-def check_solve(hist, info, ref, alts, rtol=None, min_prefix=3, check_status=True):
-    """Applies the protocol; returns a summary dict (asserts on failure)."""
+def check_solve(hist, info, ref, alts, rtol=None, min_prefix=3, check_status=True, check_restarts=False):
+    """Applies the protocol; returns a summary dict (asserts on failure).
+
+    check_restarts: also require the GPU's restart count within
+    2 * (largest alt-vs-oracle restart spread) + 2 of the oracle's (same
+    condition as the iteration band: the alternative runs agree on the status).
+    """
     r = ref.rho()
     env = envelope(ref, alts)
     g = hist[:, 0]
@@ -106,7 +111,11 @@ def check_solve(hist, info, ref, alts, rtol=None, min_prefix=3, check_status=Tru
         assert info["status"] == status, (info["status"], ref.status)
         band = 2 * spread + 0.05 * ref.iterations + 2
         assert abs(info["iterations"] - ref.iterations) <= band, (info["iterations"], ref.iterations, band)
+        if check_restarts:
+            rspread = max(abs(a.restarts - ref.restarts) for a in alts)
+            assert abs(info["restarts"] - ref.restarts) <= 2 * rspread + 2, (info["restarts"], ref.restarts, rspread)
     if rtol is not None and ref.status == "converged":
         assert info["rnorm_true"] <= rtol * info["bnorm"] * (1 + 1e-12)
     return dict(prefix=prefix, correlated=int(corr.sum()), max_strict=float(d[:prefix].max()) if prefix else 0.0,
-                iterations=(info["iterations"], ref.iterations, spread))
+                iterations=(info["iterations"], ref.iterations, spread),
+                restarts=(info.get("restarts"), getattr(ref, "restarts", None)))

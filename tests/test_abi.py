@@ -66,7 +66,7 @@ def test_invalid_arguments_rejected_without_gpu(lib):
 def test_struct_layouts():
     assert C.sizeof(pfk.OperatorDesc) == 112
     assert C.sizeof(pfk.PcDesc) == 32
-    assert C.sizeof(pfk.SolveParams) == 72
+    assert C.sizeof(pfk.SolveParams) == 80
     assert C.sizeof(pfk.SolveInfo) == 96
 
 

@@ -1,0 +1,102 @@
+"""Parity in the headline regime: the 3D variable-coefficient Poisson problem
+with eta = 10^(3 g) (smoothed Gaussian field, contrast 1e6) and the flexible
+preconditioner of 4 inner Jacobi-PCG iterations in FP64 -- the workload the
+bench times at 128^3 -- against the oracle, with the protocol of
+tests/_parity.py (strict prefix, correlated envelope region, status, iteration
+band, restart count):
+
+* PIPEFCG (Alg. 8) and PIPEGCR (Alg. 11) at 32^3 and 48^3 (correlation length
+  scaled with the grid), nu_max = 30, solved to rtol 1e-8 through the
+  residual-replacement restarts that this nonlinear preconditioner makes
+  necessary; the envelope has all four alternative oracle runs;
+* PIPEFCG and PIPEGCR at the full 128^3 size for the first 100 iterations;
+* PIPEFGMRES (Alg. 15, constant sigma) at the full 256^3 size of the
+  two-phase advection problem with the 8-sweep FP64 Chebyshev-Jacobi
+  preconditioner, the fill and 10 iterations.
+
+The oracle runs (up to five per case) are the stored envelopes of
+tests/golden/ (written by tests/golden/make_oracle_envelopes.py, oracle only)
+when this machine's inputs hash the same; otherwise they go to a pool of
+spawned worker processes as soon as the module's first test starts.
+"""
+import numpy as np
+import pytest
+
+from tests._headline_cases import CASES, SIGMA_256
+from tests._oracle_pool import envelope_runs
+from tests._parity import check_solve
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [("pipefcg", 32), ("pipefcg", 48), ("pipegcr", 32), ("pipegcr", 48)]
+FULL = ["pipefcg", "pipegcr"]
+
+
+@pytest.fixture(scope="module")
+def oracle_jobs():
+    """Every oracle envelope of the module: the stored runs of
+    tests/golden/envelope_<case>.json when the inputs hash the same here,
+    otherwise submitted to the worker pool at once (small cases first)."""
+    jobs = {}
+    for name in sorted(CASES, key=lambda k: CASES[k]["big"]):
+        cs = CASES[name]
+        jobs[name] = envelope_runs(cs["problem"], cs["method"], cs["pc"], cs["prm"], orders=cs["orders"],
+                                   big=cs["big"], stored=name)
+    return jobs
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    from paper_1511_07226_gb300 import pfk
+    return pfk.Context(0)
+
+
+def _gpu_solve(ctx, c, method, pc_kind, pc_iters, history, **kw):
+    from paper_1511_07226_gb300 import pfk
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"], c.get("vel", (0.0, 0.0, 0.0)))
+    pc = pfk.Preconditioner(ctx, op, pc_kind, inner_iters=pc_iters, precision="fp64")
+    return pfk.solve(ctx, op, pc, c["b"], method=method, mmax=30, history=history, **kw)
+
+
+@pytest.mark.parametrize("method,n", SMALL)
+def test_contrast_1e6_inner_pcg_to_convergence(ctx, oracle_jobs, method, n):
+    """The whole solve, restarts included, against the oracle's envelope."""
+    import workloads as W
+    c = W.poisson3d_gaussian(n=n, ell=8.0 * n / 128.0, log_contrast=3.0)
+    x, info, hist = _gpu_solve(ctx, c, method, "inner_pcg", 4, 20000, rtol=1e-8, maxit=20000, max_restarts=200)
+    ref, alts = oracle_jobs[f"{method}_{n}"]()
+    assert ref.status == "converged" and all(a.status == "converged" for a in alts)
+    s = check_solve(hist, info, ref, alts, rtol=1e-8, check_restarts=True)
+    assert info["status_name"] == "ok"
+    assert s["prefix"] >= 10, s
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("method", FULL)
+def test_config2_first_100_iterations(ctx, oracle_jobs, method):
+    """128^3, contrast 1e6, 4 inner FP64 Jacobi-PCG, nu_max = 30: 100
+    iterations against the oracle's envelope (pairwise and reversed orders; the
+    exactly rounded and row-sum runs cost too much at 2.1M unknowns)."""
+    import workloads as W
+    c = W.poisson3d_gaussian(n=128)
+    x, info, hist = _gpu_solve(ctx, c, method, "inner_pcg", 4, 128, rtol=1e-8, maxit=100)
+    ref, alts = oracle_jobs[f"{method}_128_first100"]()
+    assert ref.status == "maxit" and info["iterations"] == 100 == ref.iterations
+    s = check_solve(hist, info, ref, alts)
+    assert len(hist) == 101 and getattr(ref, "rho_len_full", len(ref.rho())) == 101
+    assert s["prefix"] >= 8, s
+
+
+@pytest.mark.slow
+def test_two_phase_pipefgmres_chebyshev_10_iterations(ctx, oracle_jobs):
+    """256^3 two-phase advection problem, PIPEFGMRES(30) with the 8-sweep FP64
+    Chebyshev-Jacobi preconditioner (the bench's fp64 arm), sigma fixed on both
+    sides: the fill and 10 iterations against the oracle's envelope."""
+    import workloads as W
+    c = W.poisson3d_two_phase()
+    x, info, hist = _gpu_solve(ctx, c, "pipefgmres", "chebyshev", 8, 16, rtol=1e-8, maxit=10, sigma=SIGMA_256)
+    ref, alts = oracle_jobs["pipefgmres_256_cheb_first10"]()
+    assert info["iterations"] == 10 == ref.iterations
+    s = check_solve(hist, info, ref, alts)
+    assert s["prefix"] >= 10, s
+    assert np.all(np.isfinite(hist[:, 0]))
