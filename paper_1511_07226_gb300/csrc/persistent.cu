@@ -569,7 +569,7 @@ bool persistent_eligible(const pfk_context* ctx, const pfk_operator* op, const p
   if (method != PFK_PIPEFCG && method != PFK_FCG) return false;
   if (!op->rowptr) return false;
   if (pc && pc->kind != PFK_PC_NONE && pc->kind != PFK_PC_JACOBI) return false;
-  if (pc && pc->kind == PFK_PC_JACOBI && !op->csr_dinv) return false;
+  if (pc && pc->kind == PFK_PC_JACOBI && !op->csr_dinv && !op->dinv) return false;
   return N >= 1 && N <= PFK_PERSISTENT_MAX_N && persistent_blocks(ctx, N) >= 1;
 }
 
@@ -603,7 +603,8 @@ cudaError_t launch_persistent(const SolveEnv& env, bool pipelined, int mmax, dou
   a.rowptr = op->rowptr;
   a.colidx = op->colidx;
   a.vals = op->vals;
-  a.dinv = (env.pc && env.pc->kind == PFK_PC_JACOBI) ? op->csr_dinv : nullptr;
+  // the D^-1 the Jacobi preconditioner applies (pc_apply's choice)
+  a.dinv = (env.pc && env.pc->kind == PFK_PC_JACOBI) ? (op->csr_dinv ? op->csr_dinv : op->dinv) : nullptr;
   a.N = env.N;
   a.mmax = mmax;
   a.iters = iters;

@@ -78,7 +78,8 @@ def test_ragged_and_largest_sizes(ctx, dims, method):
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"], storage="csr")
     x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), c["b"], method=method, mmax=30,
                               rtol=1e-8, maxit=maxit, history=4000, persistent="on")
-    check_solve(hist, info, ref, alts, rtol=1e-8)
+    # one unknown: the second rho is exactly 0 (relative differences undefined)
+    check_solve(hist, info, ref, alts, rtol=1e-8, min_prefix=1 if dims == (1, 1) else 3)
     if dims == (1, 1):
         assert info["iterations"] <= 1 and np.allclose(x, c["b"] / aop.diagonal())
 

@@ -49,12 +49,12 @@ def test_3d_inner_pcg(ctx, method, mmax, trunc):
     from paper_1511_07226_gb300 import pfk
     c = W.poisson3d_gaussian(dims=(20, 18, 14), ell=4.0, log_contrast=2.0, config_id=2, item_id=5)
     aop = O.StencilOperator(c["dims"], c["eta"])
-    prm = K.Params(mmax=mmax, rtol=1e-8, truncation=trunc, maxit=300)
+    prm = K.Params(mmax=mmax, rtol=1e-8, truncation=trunc, maxit=3000)
     ref, alts = oracle_with_envelope(method, aop, lambda: PC.InnerPCG(aop, 4), c["b"], prm)
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
     pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
     x, info, hist = pfk.solve(ctx, op, pc, c["b"], method=method, mmax=mmax, truncation=trunc, rtol=1e-8,
-                              maxit=300, history=4000)
+                              maxit=3000, history=4000)
     check_solve(hist, info, ref, alts, rtol=1e-8)
 
 

@@ -13,8 +13,10 @@ stresses in Sec. 6: heterogeneous viscosity, sharp inclusions, high contrast):
 
 * ``poisson2d_inclusions``  -- 64x64 cells, eta = 1e3 inside 8 random squares
   (side U{4..12}), 1 elsewhere; f ~ U(-1, 1).
-* ``poisson3d_gaussian``    -- n^3 cells, eta = 10^(3 g), g a Gaussian random
-  field with correlation length 8 cells, clipped to [-1, 1] (contrast 1e6).
+* ``poisson3d_gaussian``    -- n^3 cells, eta = 10^(3 g), g a (almost-)Gaussian
+  random field with correlation length 8 cells, clipped to [-1, 1] (contrast
+  1e6).  Generated from IEEE additions, multiplications and divisions only, so
+  the arrays are bitwise the same on every platform.
 * ``poisson3d_two_phase``   -- n^3 cells, eta = 1 with 1e4 spheres covering
   >= 20 % of the volume, constant advection velocity with global Peclet 10.
 * ``batched2d``             -- many 2D systems, sides U[32, 256], eta = 10^(2 g).
@@ -36,27 +38,94 @@ def rng(config_id: int, item_id: int = 0) -> np.random.Generator:
     return np.random.default_rng([int(config_id), int(item_id), SEED_SALT])
 
 
+# exp(x) from IEEE additions and multiplications only (the library exp and the
+# FFT differ in their last bits between platforms, and the inputs must be
+# bitwise the same on every machine that generates them): Cody-Waite reduction
+# x = k ln2 + r with the two-part ln2 of fdlibm, |r| <= ln2 / 2, a degree-13
+# Taylor polynomial of e^r by Horner's rule (truncation error < 1e-17), and an
+# exact scaling by 2^k.  Relative error ~1e-15.
+_LN2_HI = 6.93147180369123816490e-01
+_LN2_LO = 1.90821492927058770002e-10
+_INV_LN2 = 1.44269504088896338700e+00
+_LN10 = 2.30258509299404568402e+00
+
+
+def _exp_coefficients(deg: int = 13) -> list:
+    from fractions import Fraction
+    from math import factorial
+    return [float(Fraction(1, factorial(j))) for j in range(deg + 1)]
+
+
+_EXP_C = _exp_coefficients()
+
+
+def portable_exp(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    k = np.rint(x * _INV_LN2)
+    r = (x - k * _LN2_HI) - k * _LN2_LO
+    p = np.full_like(r, _EXP_C[-1])
+    for c in reversed(_EXP_C[:-1]):
+        p = p * r + c
+    return np.ldexp(p, k.astype(np.int32))
+
+
+def portable_pow10(x) -> np.ndarray:
+    """10^x = exp(x ln 10) with portable_exp."""
+    return portable_exp(np.asarray(x, dtype=np.float64) * _LN10)
+
+
+def box_widths(sigma: float, passes: int = 4) -> list:
+    """Odd widths of `passes` box filters whose repeated application has
+    (close to) the variance sigma^2 of a Gaussian kernel: Kovesi's rule (Fast
+    almost-Gaussian filtering, 2010) -- m passes of width wl and the rest of
+    width wl + 2, wl the largest odd width not above the ideal one."""
+    ideal = np.sqrt(12.0 * sigma * sigma / passes + 1.0)
+    wl = int(np.floor(ideal))
+    if wl % 2 == 0:
+        wl -= 1
+    wl = max(wl, 1)
+    wu = wl + 2
+    m = int(round((12.0 * sigma * sigma - passes * wl * wl - 4 * passes * wl - 3 * passes) / (-4.0 * wl - 4.0)))
+    m = min(max(m, 0), passes)
+    return [wl] * m + [wu] * (passes - m)
+
+
+def _box_periodic(f: np.ndarray, axis: int, width: int) -> np.ndarray:
+    """Periodic moving average of odd `width` along `axis`, from a running sum
+    (numpy.cumsum adds strictly in order, so the result is the same on every
+    platform)."""
+    if width <= 1:
+        return f
+    half = width // 2
+    n = f.shape[axis]
+    idx = np.arange(-half - 1, n + half) % n
+    padded = np.take(f, idx, axis=axis)
+    cs = np.cumsum(padded, axis=axis)
+    hi = np.take(cs, np.arange(width, width + n), axis=axis)
+    lo = np.take(cs, np.arange(0, n), axis=axis)
+    return (hi - lo) / float(width)
+
+
 def gaussian_field(shape, ell: float, g: np.random.Generator) -> np.ndarray:
-    """White N(0,1) noise filtered by a periodic Gaussian kernel.
+    """White N(0,1) noise smoothed by an almost-Gaussian periodic filter.
 
     Covariance exp(-r^2 / (2 ell^2)) needs a kernel of std ell/sqrt(2); the
-    filter is applied in Fourier space, then the field is normalised to zero
-    mean and unit sample std and clipped to [-1, 1].
+    kernel is approximated by four passes of periodic box filters per axis
+    whose combined variance is (close to) ell^2 / 2 (box_widths).  The field is
+    then normalised to zero mean and unit sample std and clipped to [-1, 1].
+    Every step is additions, multiplications and divisions in a fixed order,
+    so the field is bitwise the same on every platform.
     """
     w = g.standard_normal(shape)
     s = ell / np.sqrt(2.0)
-    fw = np.fft.fftn(w)
-    for ax, n in enumerate(shape):
-        k = 2.0 * np.pi * np.fft.fftfreq(n)
-        filt = np.exp(-0.5 * (k * s) ** 2)
-        bshape = [1] * len(shape)
-        bshape[ax] = n
-        fw *= filt.reshape(bshape)
-    f = np.real(np.fft.ifftn(fw))
-    f -= f.mean()
+    f = w
+    for ax in range(len(shape)):
+        for width in box_widths(s):
+            f = _box_periodic(f, ax, width)
+    f = f - f.mean()
     sd = f.std()
     if sd > 0:
-        f /= sd
+        f = f / sd
     return np.clip(f, -1.0, 1.0)
 
 
@@ -85,7 +154,7 @@ def poisson3d_gaussian(n: int = 128, ell: float = 8.0, log_contrast: float = 3.0
     nx, ny, nz = dims if dims is not None else (n, n, n)
     g = rng(config_id, item_id)
     field = gaussian_field((nz, ny, nx), ell, g)
-    eta = np.power(10.0, log_contrast * field)
+    eta = portable_pow10(log_contrast * field)
     b = _rhs((nz, ny, nx), g, nx)
     return dict(dims=(nx, ny, nz), eta=eta.reshape(-1).copy(), b=b, vel=(0.0, 0.0, 0.0))
 
@@ -124,7 +193,7 @@ def batched2d_system(index: int, side: int, ell: float = 8.0, log_contrast: floa
                      config_id: int = 4) -> dict:
     g = rng(config_id, index)
     field = gaussian_field((side, side), ell, g)
-    eta = np.power(10.0, log_contrast * field)
+    eta = portable_pow10(log_contrast * field)
     b = _rhs((side, side), g, side)
     return dict(dims=(side, side, 1), eta=eta.reshape(-1).copy(), b=b, vel=(0.0, 0.0, 0.0))
 
