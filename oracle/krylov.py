@@ -152,11 +152,16 @@ class _Monitor:
         return False
 
 
+def axpy(y: np.ndarray, a: float, v: np.ndarray) -> np.ndarray:
+    """y + a v (every vector update of the methods goes through here)."""
+    return y + a * v
+
+
 def _maxpy(base: np.ndarray, beta: dict, hist: dict) -> np.ndarray:
     """base + sum_k beta_k hist_k, k ascending."""
     out = base.copy()
     for k in sorted(beta):
-        out = out + beta[k] * hist[k]
+        out = axpy(out, beta[k], hist[k])
     return out
 
 
@@ -191,8 +196,8 @@ def pcg(A, M, b, x0, prm: Params) -> Result:
             if res.iterations >= prm.maxit:
                 return mon.finish(x, "maxit")
             i += 1
-            x = x + alpha * p
-            r = r - alpha * s
+            x = axpy(x, alpha, p)
+            r = axpy(r, -alpha, s)
             res.iterations += 1
             u = M(r)
             gamma_new = dot(u, r)
@@ -205,7 +210,7 @@ def pcg(A, M, b, x0, prm: Params) -> Result:
                 break
             beta = gamma_new / gamma
             gamma = gamma_new
-            p = u + beta * p
+            p = axpy(u, beta, p)
             s = A(p)
             eta = dot(s, p)
             res.history[-1].update(eta=eta, beta=beta)
@@ -247,8 +252,8 @@ def fcg(A, B, b, x0, prm: Params) -> Result:
             if res.iterations >= prm.maxit:
                 return mon.finish(x, "maxit")
             i += 1
-            x = x + alpha * P[i - 1]
-            r = r - alpha * S[i - 1]
+            x = axpy(x, alpha, P[i - 1])
+            r = axpy(r, -alpha, S[i - 1])
             res.iterations += 1
             u = B(r)
             gamma = dot(u, r)
@@ -306,8 +311,8 @@ def cgfcg(A, B, b, x0, prm: Params) -> Result:
             if res.iterations >= prm.maxit:
                 return mon.finish(x, "maxit")
             i += 1
-            x = x + alpha * P[i - 1]
-            r = r - alpha * S[i - 1]
+            x = axpy(x, alpha, P[i - 1])
+            r = axpy(r, -alpha, S[i - 1])
             res.iterations += 1
             u = B(r)
             w = A(u)
@@ -379,10 +384,10 @@ def pipefcg(A, B, b, x0, prm: Params, naive: bool = False, theta: bool = False) 
             if res.iterations >= prm.maxit:
                 return mon.finish(x, "maxit")
             i += 1
-            x = x + alpha * P[i - 1]
-            r = r - alpha * S[i - 1]
-            u = u - alpha * Q[i - 1]
-            w = w - alpha * Z[i - 1]
+            x = axpy(x, alpha, P[i - 1])
+            r = axpy(r, -alpha, S[i - 1])
+            u = axpy(u, -alpha, Q[i - 1])
+            w = axpy(w, -alpha, Z[i - 1])
             res.iterations += 1
             gamma = dot(u, r)
             nu = nu_window(i, prm)
@@ -399,7 +404,7 @@ def pipefcg(A, B, b, x0, prm: Params, naive: bool = False, theta: bool = False) 
                 m = B(w)
             elif theta:
                 th = dot(r, w) / dot(r, r)
-                m = th * u + B(w - th * r)
+                m = axpy(B(axpy(w, -th, r)), th, u)
             else:
                 m = u + B(w - r)
             n = A(m)
@@ -455,8 +460,8 @@ def gcr(A, B, b, x0, prm: Params) -> Result:
             if res.iterations >= prm.maxit:
                 return mon.finish(x, "maxit")
             i += 1
-            x = x + alpha * P[i - 1]
-            r = r - alpha * S[i - 1]
+            x = axpy(x, alpha, P[i - 1])
+            r = axpy(r, -alpha, S[i - 1])
             res.iterations += 1
             u = B(r)
             au = A(u)
@@ -513,11 +518,11 @@ def _pipegcr(A, B, b, x0, prm: Params, w_recurred: bool) -> Result:
             if res.iterations >= prm.maxit:
                 return mon.finish(x, "maxit")
             i += 1
-            x = x + alpha * P[i - 1]
-            r = r - alpha * S[i - 1]
-            u = u - alpha * Q[i - 1]
+            x = axpy(x, alpha, P[i - 1])
+            r = axpy(r, -alpha, S[i - 1])
+            u = axpy(u, -alpha, Q[i - 1])
             if w_recurred:
-                w = w - alpha * Z[i - 1]
+                w = axpy(w, -alpha, Z[i - 1])
             else:
                 w = A(u)
             res.iterations += 1
@@ -610,7 +615,7 @@ def fgmres(A, B, b, x0, prm: Params) -> Result:
                 H[j, i - 1] = dot(P[j], z)
             pbar = z.copy()
             for j in range(i):
-                pbar = pbar - P[j] * H[j, i - 1]
+                pbar = axpy(pbar, -H[j, i - 1], P[j])
             H[i, i - 1] = float(np.linalg.norm(pbar))
             res.iterations += 1
             ncols = i
@@ -667,7 +672,7 @@ def _fgmres_single_reduction(A, B, b, x0, prm: Params, pipelined: bool) -> Resul
             continue
         P = [r0 / beta0]                  # p_0
         U = [B(P[0])]                     # u_0 (first column of tilde-U)
-        Zb = [A(U[0]) - sigma * P[0]]     # zbar_0
+        Zb = [axpy(A(U[0]), -sigma, P[0])]     # zbar_0
         if pipelined:
             qb = B(Zb[0])                 # qbar_0
             wb = A(qb)                    # wbar_0
@@ -701,22 +706,22 @@ def _fgmres_single_reduction(A, B, b, x0, prm: Params, pipelined: bool) -> Resul
             hb = Hb[i, i - 1]
             pi = Zb[i - 1].copy()
             for k in range(i):
-                pi = pi - Hb[k, i - 1] * P[k]
+                pi = axpy(pi, -Hb[k, i - 1], P[k])
             P.append(pi / hb)
             if pipelined:
                 ui = qb.copy()
                 for k in range(i):
-                    ui = ui - U[k] * Hb[k, i - 1]
+                    ui = axpy(ui, -Hb[k, i - 1], U[k])
                 U.append(ui / hb)
                 zi = wb.copy()
                 for k in range(i):
-                    zi = zi - H[k, i - 1] * Zb[k]
+                    zi = axpy(zi, -H[k, i - 1], Zb[k])
                 Zb.append(zi / H[i, i - 1])
                 qb = B(Zb[i])
                 wb = A(qb)
             else:
                 U.append(B(P[i]))
-                Zb.append(A(U[i]) - sigma * P[i])
+                Zb.append(axpy(A(U[i]), -sigma, P[i]))
         if ncols:
             y, _ = _lsq(H[:ncols + 1, :ncols], beta0)
             if prm.trace:

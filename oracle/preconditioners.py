@@ -98,6 +98,11 @@ def _dot(a, b) -> float:
     return float(np.dot(np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)))
 
 
+def _axpy(y, a, v):
+    """y + a v (the vector updates of the inner iterations go through here)."""
+    return y + a * v
+
+
 class IdentityPC:
     linear = True
 
@@ -183,17 +188,17 @@ class InnerPCG:
             return x.astype(np.float64)
         alpha = gamma / eta
         for i in range(1, self.k + 1):
-            x = (x + dt(alpha) * p).astype(dt)
+            x = _axpy(x, dt(alpha), p).astype(dt)
             if i == self.k:
                 break
-            r = (r - dt(alpha) * s).astype(dt)
+            r = _axpy(r, -dt(alpha), s).astype(dt)
             u = (self.dinv * r).astype(dt)
             gamma_new = _dot(u, r)
             if gamma_new == 0.0:
                 break
             beta = gamma_new / gamma
             gamma = gamma_new
-            p = (u + dt(beta) * p).astype(dt)
+            p = _axpy(u, dt(beta), p).astype(dt)
             s = self.apply_A(p).astype(dt)
             eta = _dot(s, p)
             if eta == 0.0:
@@ -252,7 +257,7 @@ class Chebyshev:
                 break
             r = (r - self.apply_A(d)).astype(dt)
             rho_new = 1.0 / (2.0 * sigma1 - rho)
-            d = (dt(rho_new * rho) * d + dt(2.0 * rho_new / delta) * (self.dinv * r)).astype(dt)
+            d = _axpy(dt(2.0 * rho_new / delta) * (self.dinv * r), dt(rho_new * rho), d).astype(dt)
             rho = rho_new
         return x.astype(np.float64)
 

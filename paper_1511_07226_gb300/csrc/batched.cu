@@ -252,8 +252,9 @@ __device__ void sys_pc(const BatchSys& S, const BatchParams& P, const double* v,
                        double* smem, BlkState* st) {
   if (P.pc_kind == PFK_PC_NONE || P.pc_kind == PFK_PC_JACOBI) {
     SYS_ELEMS(S.n, e) {
-      const double y = P.pc_kind == PFK_PC_JACOBI ? S.dinv[e] * v[e] : v[e];
-      out[e] = add ? add[e] + y : y;
+      // B(v) = D^-1 v and add + B(v): two roundings (no fused multiply-add)
+      const double y = P.pc_kind == PFK_PC_JACOBI ? __dmul_rn(S.dinv[e], v[e]) : v[e];
+      out[e] = add ? __dadd_rn(add[e], y) : y;
     }
     __syncthreads();
     return;

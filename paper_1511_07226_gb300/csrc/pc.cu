@@ -66,9 +66,11 @@ __global__ void __launch_bounds__(kThreads) jacobi_kernel(const double* __restri
                                                           const double* __restrict__ add, double* __restrict__ out,
                                                           int64_t n, const int* __restrict__ status) {
   SKIP_IF_DONE(status);
+  // product and sum rounded separately (no fused multiply-add), as B(v) = D^-1 v
+  // and add + B(v) are two operations
   GRID_LOOP(c, n) {
-    double y = dinv ? dinv[c] * v[c] : v[c];
-    out[c] = add ? add[c] + y : y;
+    double y = dinv ? __dmul_rn(dinv[c], v[c]) : v[c];
+    out[c] = add ? __dadd_rn(add[c], y) : y;
   }
 }
 

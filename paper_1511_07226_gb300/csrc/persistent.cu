@@ -42,6 +42,7 @@ constexpr int kPerThreads = 128;
 constexpr int kPerRows = 32;                // rows of a chunk (4 threads per row)
 constexpr int kPerNd = PFK_MAX_MMAX + 4;    // largest partial row (gamma, delta, ||r||^2, c_{i-1}, window)
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+constexpr int kMaxPerBlocks = 192;          // grid cap (the partial rows live in shared memory: 54 KB)
 
 struct PersistArgs {
   const int32_t* rowptr;
@@ -123,15 +124,33 @@ __device__ __forceinline__ double quad_col_sum(double v) {
   return v;
 }
 
-// Combines the block rows partials[b * kPerNd + j], b < nb, j < nd, in a fixed
+// Copies the block rows partials[0 .. nb * kPerNd) (16-byte aligned, a
+// multiple of 16 bytes) into shared memory with asynchronous 16-byte copies
+// issued by all threads at once (cp.async, completed by wait_partials), so one
+// L2 round trip brings every row instead of one per load.
+__device__ __forceinline__ void fetch_partials(const double* partials, int nb, double* s_part) {
+  const int chunks = nb * (kPerNd / 2);
+  for (int c = threadIdx.x; c < chunks; c += kPerThreads) {
+    const unsigned int dst = (unsigned int)__cvta_generic_to_shared(s_part + 2 * c);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(partials + 2 * c) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void wait_partials() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+}
+
+// Sums the fetched rows s_part[b * kPerNd + j], b < nb, j < nd, in a fixed
 // order (lane l of warp w: rows l, l + 32, ... of columns w, w + 4, ..., then a
 // fixed shuffle tree) into out[j] (shared memory).  Every block that calls it
 // gets bitwise the same sums.
-__device__ __forceinline__ void combine_rows(const double* partials, int nb, int nd, double* out) {
+__device__ __forceinline__ void sum_partials(const double* s_part, int nb, int nd, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = warp; j < nd; j += kPerThreads / 32) {
     double a = 0.0;
-    for (int b = lane; b < nb; b += 32) a += __ldcg(&partials[(size_t)b * kPerNd + j]);
+    for (int b = lane; b < nb; b += 32) a += s_part[b * kPerNd + j];
     a = warp_sum(a);
     if (lane == 0) out[j] = a;
   }
@@ -241,6 +260,7 @@ __device__ __forceinline__ double csr_row(const PersistArgs& a, const double* m,
 template <int NW>
 __global__ void __launch_bounds__(kPerThreads) pipefcg_persistent(PersistArgs a) {
   constexpr int NWQ = NW / 4;
+  extern __shared__ double s_part[];     // the grid's partial rows, nb * kPerNd
   __shared__ PerState st;
   __shared__ double s_red[(kPerThreads / 32) * kPerNd];
   __shared__ size_t s_off[NW];
@@ -306,7 +326,7 @@ __global__ void __launch_bounds__(kPerThreads) pipefcg_persistent(PersistArgs a)
         const double un = fma(-alpha, qv, u0);
         const double wn = fma(-alpha, z, w0);
         const double t = wn - rn;                            // B's input w_i - r_i (eq. BwMinusR)
-        const double y = a.dinv ? __ldcg(&a.dinv[e]) * t : t;
+        const double y = a.dinv ? __dmul_rn(__ldcg(&a.dinv[e]), t) : t;
         if (q == 0) {
           a.P[coff + e] = p;
           a.S[coff + e] = s;
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(kPerThreads) pipefcg_persistent(PersistArgs a)
           a.r[e] = rn;
           a.u[e] = un;
           a.w[e] = wn;
-          mnew[e] = un + y;                                  // m_i = u_i + B(w_i - r_i)
+          mnew[e] = __dadd_rn(un, y);                        // m_i = u_i + B(w_i - r_i)
           sc[0] = fma(un, rn, sc[0]);
           sc[1] = fma(un, wn, sc[1]);
           sc[2] = fma(rn, rn, sc[2]);
@@ -333,12 +353,15 @@ __global__ void __launch_bounds__(kPerThreads) pipefcg_persistent(PersistArgs a)
       return;
     }
 
-    // ---- n_i = A m_i (own rows), then the combine of the pass's reduction ----
+    // ---- the pass's partial rows in flight while n_i = A m_i (own rows) is
+    // formed, then their combine ----
+    fetch_partials(part, nb, s_part);
     for (int c = blockIdx.x; c < a.nchunks; c += nb) {
       const int64_t e = (int64_t)c * kPerRows + rowi;
       if (e < N && q == 0) a.n[e] = csr_row(a, mnew, e);
     }
-    combine_rows(part, nb, 4 + nwp, st.sums);
+    wait_partials();
+    sum_partials(s_part, nb, 4 + nwp, st.sums);
 
     // ---- scalar phase of iteration i (Alg. 8), the same in every block ----
     const int nu = nu_window(i, a.mmax, ctl->truncation);
@@ -410,6 +433,7 @@ __global__ void __launch_bounds__(kPerThreads) pipefcg_persistent(PersistArgs a)
 template <int NW>
 __global__ void __launch_bounds__(kPerThreads) fcg_persistent(PersistArgs a) {
   constexpr int NWQ = NW / 4;
+  extern __shared__ double s_part[];     // the grid's partial rows, nb * kPerNd
   __shared__ PerState st;
   __shared__ double s_red[(kPerThreads / 32) * kPerNd];
   __shared__ size_t s_off[NW];
@@ -461,7 +485,9 @@ __global__ void __launch_bounds__(kPerThreads) fcg_persistent(PersistArgs a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->status = kTimeout;
       return;
     }
-    combine_rows(red1, nb, 4 + nu, st.sums);
+    fetch_partials(red1, nb, s_part);
+    wait_partials();
+    sum_partials(s_part, nb, 4 + nu, st.sums);
     // Alg. 2: gamma_i, convergence, beta_{i,k} = -<u_i, s_k> / eta_k
     if (threadIdx.x == 0) {
       const double gamma = st.sums[0], rr = st.sums[1];
@@ -526,7 +552,9 @@ __global__ void __launch_bounds__(kPerThreads) fcg_persistent(PersistArgs a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->status = kTimeout;
       return;
     }
-    combine_rows(red3, nb, 1, st.sums);
+    fetch_partials(red3, nb, s_part);
+    wait_partials();
+    sum_partials(s_part, nb, 1, st.sums);
     if (threadIdx.x == 0) {
       // Alg. 2: eta_i = <p_i, s_i>, alpha_i = gamma_i / eta_i
       const double eta = st.sums[0];
@@ -560,7 +588,8 @@ int persistent_template(int mmax) { return mmax <= 4 ? 4 : mmax <= 8 ? 8 : mmax 
 // SM's FP64 units in use and the barrier short).
 int persistent_blocks(const pfk_context* ctx, int64_t N) {
   const int64_t chunks = (N + kPerRows - 1) / kPerRows;
-  return (int)(chunks < ctx->num_sms ? chunks : ctx->num_sms);
+  const int64_t cap = ctx->num_sms < kMaxPerBlocks ? ctx->num_sms : kMaxPerBlocks;
+  return (int)(chunks < cap ? chunks : cap);
 }
 
 bool persistent_eligible(const pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc, int method, int naive_like,
@@ -580,10 +609,14 @@ int64_t persistent_partials(const pfk_context* ctx, int64_t N) {
 template <int NW>
 static cudaError_t launch_one(bool pipelined, const PersistArgs& a, int blocks, cudaStream_t st) {
   void* fn = pipelined ? (void*)pipefcg_persistent<NW> : (void*)fcg_persistent<NW>;
+  const int smem = blocks * kPerNd * (int)sizeof(double);
+  cudaError_t e = pipelined ? cudaFuncSetAttribute(pipefcg_persistent<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                            : cudaFuncSetAttribute(fcg_persistent<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kPerThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -612,9 +645,11 @@ cudaError_t launch_persistent(const SolveEnv& env, bool pipelined, int mmax, dou
   a.x = x; a.r = r; a.u = u; a.w = w; a.m0 = m0; a.m1 = m1; a.n = n;
   a.P = P; a.S = S; a.Q = Q; a.Z = Z;
   a.ctl = env.ctl;
-  a.partials = env.partials;
+  // partial rows start on a 16-byte boundary (asynchronous 16-byte copies)
+  const size_t mis = ((uintptr_t)env.partials & 15u) / sizeof(double);
+  a.partials = env.partials + (mis ? 2 - mis : 0);
   const int blocks = persistent_blocks(env.ctx, env.N);
-  if (!env.partials_fit(2 * blocks, kPerNd)) return cudaErrorInvalidValue;
+  if (!env.partials_fit(2 * blocks + 1, kPerNd)) return cudaErrorInvalidValue;
   switch (persistent_template(mmax)) {
     case 4: return launch_one<4>(pipelined, a, blocks, env.st);
     case 8: return launch_one<8>(pipelined, a, blocks, env.st);

@@ -6,8 +6,8 @@ Each case: the workload generator and its arguments, the method, the
 preconditioner, the oracle parameters and the summation orders of its
 envelope (the first is the reference run).
 """
-ALL_ORDERS = ("numpy", "pairwise", "reversed", "fsum", "rowsum")
-FAST_ORDERS = ("numpy", "pairwise", "reversed")
+ALL_ORDERS = ("numpy", "pairwise", "reversed", "fsum", "fma", "rowsum")
+FAST_ORDERS = ("numpy", "pairwise", "reversed", "fma")
 SIGMA_256 = 1.0
 
 

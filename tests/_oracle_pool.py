@@ -97,6 +97,10 @@ def _run(job: dict) -> dict:
     if f is not None:
         K.dot = f
         PC._dot = f
+    if job["order"] == "fma":
+        from tests._parity import fma_axpy
+        K.axpy = fma_axpy
+        PC._axpy = fma_axpy
     kind, args = job["pc"]
     lo, hi = PC.chebyshev_bounds(A) if kind == "chebyshev" else (None, None)
     if job["order"] == "rowsum":

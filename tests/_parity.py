@@ -8,11 +8,15 @@ summation order of its inner products, shows the size of that drift.  The
 protocol is therefore:
 
 1. Envelope: the oracle is re-run with three other summation orders of every
-   inner product (pairwise, reversed, exactly rounded via math.fsum) and, for
-   a stencil operator, once more with the operator applied in row-sum form
-   (its assembled CSR: d_i u_i - sum K u_nbr, the form the GPU evaluates)
-   instead of the flux form sum K (u_i - u_nbr); env_i is the running maximum
-   over those runs of |rho_alt - rho| / rho at entry i.
+   inner product (pairwise, reversed, exactly rounded via math.fsum), once
+   with every vector update y + a v evaluated as a fused multiply-add (the
+   product kept exact, one rounding: how the GPU kernels evaluate their AXPYs
+   and MAXPYs, and what sets the gap between the recurred and the true
+   residual, hence when a residual replacement fires) and, for a stencil
+   operator, once more with the operator applied in row-sum form (its
+   assembled CSR: d_i u_i - sum K u_nbr, the form the GPU evaluates) instead
+   of the flux form sum K (u_i - u_nbr); env_i is the running maximum over
+   those runs of |rho_alt - rho| / rho at entry i.
 2. Strict prefix: on every entry where env_i <= 1e-11 the GPU must agree with
    the oracle to 1e-10 relative.
 3. Envelope region: while env_i <= 1e-4 (the trajectories are still
@@ -54,18 +58,52 @@ def _alt_dots():
     return [pairwise, reversed_, exact]
 
 
+_SPLIT = 134217729.0   # 2^27 + 1: Dekker's splitting constant for float64
+
+
+def fma_axpy(y, a, v):
+    """y + a v with the product kept exact before the addition (Dekker's
+    TwoProduct and Knuth's TwoSum, then one final rounding): the fused
+    multiply-add evaluation of an update, up to a rare double rounding.  Float32
+    arrays keep the plain evaluation."""
+    y = np.asarray(y)
+    v = np.asarray(v)
+    if y.dtype != np.float64 or v.dtype != np.float64:
+        return y + a * v
+    a = np.float64(a)
+    p = a * v
+    c = _SPLIT * a
+    ah = c - (c - a)
+    al = a - ah
+    c = _SPLIT * v
+    vh = c - (c - v)
+    vl = v - vh
+    e = ((ah * vh - p) + ah * vl + al * vh) + al * vl
+    s_ = p + y
+    bb = s_ - p
+    t = (p - (s_ - bb)) + (y - bb)
+    return s_ + (t + e)
+
+
 def oracle_with_envelope(method, A, make_B, b, prm, x0=None):
-    """(reference result, [alternative-order results])."""
+    """(reference result, [alternative results]): three other summation orders
+    of every inner product, every vector update evaluated as a fused
+    multiply-add (as the GPU kernels evaluate theirs), and, for a stencil, the
+    operator in row-sum form."""
     ref = K.solve(method, A, make_B(), b, x0=x0, prm=prm)
     alts = []
-    saved = (K.dot, PC._dot)
+    saved = (K.dot, PC._dot, K.axpy, PC._axpy)
     try:
         for f in _alt_dots():
             K.dot = f
             PC._dot = f
             alts.append(K.solve(method, A, make_B(), b, x0=x0, prm=prm))
+        K.dot, PC._dot = saved[0], saved[1]
+        K.axpy = fma_axpy
+        PC._axpy = fma_axpy
+        alts.append(K.solve(method, A, make_B(), b, x0=x0, prm=prm))
     finally:
-        K.dot, PC._dot = saved
+        K.dot, PC._dot, K.axpy, PC._axpy = saved
     if hasattr(A, "to_csr"):
         alts.append(K.solve(method, A.to_csr(), make_B(), b, x0=x0, prm=prm))
     return ref, alts

@@ -21,6 +21,7 @@ the oracle's own range.  Orders:
   pairwise  numpy.sum of the products (pairwise summation),
   reversed  numpy.dot over the reversed vectors,
   fsum      exactly rounded sums (math.fsum) -- slow, small sizes only,
+  fma       every vector update y + a v evaluated as a fused multiply-add,
   rowsum    the operator as its assembled CSR (d_i u_i - sum K u_nbr).
 
 Usage: python tests/golden/make_oracle_spread.py --n 64 --ell 4 --methods pipefcg,pipegcr
@@ -39,7 +40,7 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 
-ALL_ORDERS = ("numpy", "pairwise", "reversed", "fsum", "rowsum")
+ALL_ORDERS = ("numpy", "pairwise", "reversed", "fsum", "fma", "rowsum")
 
 
 def spread_path(n: int, method: str) -> str:
@@ -70,6 +71,10 @@ def one_run(job: dict) -> dict:
     if f is not None:
         K.dot = f
         PC._dot = f
+    if job["order"] == "fma":
+        from tests._parity import fma_axpy
+        K.axpy = fma_axpy
+        PC._axpy = fma_axpy
     op = A.to_csr() if job["order"] == "rowsum" else A
     prm = K.Params(mmax=30, rtol=1e-8, maxit=job["maxit"], max_restarts=job["max_restarts"])
     t0 = time.perf_counter()

@@ -55,7 +55,10 @@ def test_3d_inner_pcg(ctx, method, mmax, trunc):
     pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
     x, info, hist = pfk.solve(ctx, op, pc, c["b"], method=method, mmax=mmax, truncation=trunc, rtol=1e-8,
                               maxit=3000, history=4000)
-    check_solve(hist, info, ref, alts, rtol=1e-8)
+    # Alg. 7 with a nonlinear preconditioner stagnates (Sec. 3.2.1): whether and
+    # when it reaches rtol is decided by rounding alone (the oracle's own
+    # summation orders disagree), so only the correlated part is compared
+    check_solve(hist, info, ref, alts, rtol=1e-8, check_status=method != "pipefcg_naive")
 
 
 def test_unpreconditioned_norm_and_maxit(ctx):
