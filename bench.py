@@ -40,11 +40,13 @@ METRIC = "PIPEFCG 128^3 time-to-1e-8 & HBM GB/s vs FP64 plain; serve p50/p99 lat
 UNIT = "solves/s"
 WORKLOAD = "PIPEFCG nu_max=30, 3D 128^3 variable-coefficient Poisson (contrast 1e6), 4 inner Jacobi-PCG (FP64), rtol 1e-8"
 
-# FP64 FMA peak of GB300: 2 FP64 FMA per clock per SM x 152 SMs x 2 flops x
-# 2.07 GHz maximum SM clock = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s; a
-# dependent-FMA probe measured 1.19).  The fused pass does ~1.2 FP64 FMA per
-# 8-byte word it moves, above the HBM balance point of ~0.4, so it is bound by
-# this FP64 pipe, not by HBM.
+# FP64 FMA peak of GB300 from unit counts and clocks: 2 FP64 FMA per clock per
+# SM x 152 SMs x 2 flops x 2.07 GHz maximum SM clock = 1.259 TFLOP/s (the
+# nominal 1.25 TFLOP/s).  The FMA-chain probe (pfk_probe_fp64_fma, `bench.py
+# --fp64-probe`, profiles/fp64_peak.md) measures 1.057 TFLOP/s at 2.07 GHz;
+# every line reports it beside the roofline (`fp64_probe`).  The fused pass
+# does ~1.2 FP64 FMA per 8-byte word it moves, above the HBM balance point of
+# ~0.4, so it is bound by this FP64 pipe, not by HBM.
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic per launch of the fused pass from the committed ncu summary
@@ -69,6 +71,10 @@ def max_over_ranks(x: float, dist, device) -> float:
 def replica_value(world: int, ms_max: float) -> float:
     """Whole-job solves/s of `world` replicas, each taking at most ms_max per solve."""
     return world * 1e3 / ms_max
+
+
+def peak_hbm_gbs() -> float:
+    return float(measured_peaks().get("hbm_gbs", 6800.0))
 
 
 def measured_peaks() -> dict:
@@ -244,17 +250,39 @@ def main():
     ap.add_argument("--maxit", type=int, default=10000)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--method", default="pipefcg", help="method of the --ncu-case solve")
-    ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase", "batched"],
+    ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase", "batched", "config1"],
                     help="--ncu-case problem: Gaussian-field Poisson (4 inner PCG), two-phase advection "
-                         "(8 Chebyshev sweeps), or the first --n systems of the batched workload")
+                         "(8 Chebyshev sweeps), the first --n systems of the batched workload, or the 64x64 CSR "
+                         "problem with Jacobi (--method pipefcg or fcg, persistent path; --maxit iterations)")
+    ap.add_argument("--fp64-probe", action="store_true",
+                    help="only the FP64 FMA-rate probe (pfk_probe_fp64_fma), three times, as JSON")
     ap.add_argument("--block-threads", type=int, default=256,
                     help="threads per block of the --case batched profiler case")
-    ap.add_argument("--extras", default="config1,fcg,pipegcr,nu_sweep,stokes,batched,fgmres256,serve",
+    ap.add_argument("--extras", default="config1,fcg,pipegcr,nu_sweep,stokes,batched,fgmres256,serve,serve_sweep",
                     help="comma-separated secondary measurements (config1, fcg, pipegcr, nu_sweep, stokes, batched, "
-                         "fgmres256, serve; serve_sweep is opt-in) or 'none'")
+                         "fgmres256, serve, serve_sweep) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
+    if args.fp64_probe:
+        from paper_1511_07226_gb300 import pfk
+        ctx = pfk.Context(0)
+        runs = [pfk.probe_fp64_fma(ctx, 1 << 17) for _ in range(3)]
+        print(json.dumps({"fp64_probe_tflops": [r["tflops"] for r in runs], "ms": [r["ms"] for r in runs],
+                          "derived_peak_tflops": FP64_PEAK_TFLOPS}))
+        return
+    if args.ncu_case and args.case == "config1":
+        import workloads as W
+        from paper_1511_07226_gb300 import pfk
+        ctx = pfk.Context(0)
+        c = W.poisson2d_inclusions()
+        op = pfk.Operator.stencil(ctx, c["dims"], c["eta"], storage="csr")
+        pc = pfk.Preconditioner(ctx, op, "jacobi")
+        _, info, _ = pfk.solve(ctx, op, pc, c["b"], method=args.method, mmax=30, rtol=1e-8, maxit=args.maxit,
+                               persistent="on")
+        print(json.dumps({"ncu_case": "config1", "method": args.method, "iterations": info["iterations"],
+                          "status": info["status_name"]}))
+        return
     if args.ncu_case and args.case == "batched":
         import workloads as W
         from paper_1511_07226_gb300 import pfk
@@ -576,6 +604,25 @@ def extra_batched(ctx, dev, args) -> dict:
     kern_ms = max(i["time_ms"] for i in infos)
     unknowns = int(sum(int(s) ** 2 for s in sides))
     conv = int(sum(i["status_name"] == "ok" for i in infos))
+    # the same batch with restart-style truncation (Sec. 5 remark): the
+    # truncation the 128^3 sweep shows curing most of the stagnation
+    rinfos = pfk.solve_batched(ctx, ops, bs, **dict(kw, truncation="restart"))[1]
+    rkern = max(i["time_ms"] for i in rinfos)
+    rconv = int(sum(i["status_name"] == "ok" for i in rinfos))
+    restart_trunc = {"converged": rconv, "converged_fraction": rconv / len(ops), "kernel_ms": rkern,
+                     "solves_per_s": rconv / (rkern / 1e3),
+                     "system_iterations_per_s": float(sum(i["iterations"] for i in rinfos)) / (rkern / 1e3),
+                     "iterations_median": int(np.median([i["iterations"] for i in rinfos])),
+                     "max_true_rel_residual": float(max(i["rnorm_true"] / i["bnorm"] for i in rinfos))}
+    # algorithmic bytes per unknown and system-iteration (config 4: 2D 5-point,
+    # nu = 20, 4 inner CG iterations in FP32): the fused pass 4 nu + 15 FP64
+    # words, the operator 5 (m, d, kx, ky read, n written); per inner CG
+    # iteration 15 FP32 words (s = A p: p, d, kx, ky, s; r update: r, s, D^-1,
+    # r; x, p updates: x, p, r, D^-1, x, p), plus 2 for the final x
+    bytes_it = 8.0 * (4 * 20 + 15 + 5) + 4.0 * (4 * 15 + 2)
+    mean_n = unknowns / len(ops)
+    hbm = peak_hbm_gbs()
+    achieved = float(sum(i["iterations"] * int(sides[j]) ** 2 for j, i in enumerate(infos))) * bytes_it / (kern_ms / 1e3) / 1e9
     return {"workload": "512 2D systems, sides U[32,256], contrast 1e4, PIPEFCG nu_max=20, 4 inner CG (FP32), "
                         f"at most {BATCHED_MAXIT} iterations per system",
             "systems": len(ops), "unknowns": unknowns, "kernel_ms": kern_ms,
@@ -587,7 +634,11 @@ def extra_batched(ctx, dev, args) -> dict:
             "iterations_median": int(np.median([i["iterations"] for i in infos])),
             "iterations_max": int(max(i["iterations"] for i in infos)),
             "restarts_median": int(np.median([i["restarts"] for i in infos])),
-            "max_true_rel_residual": float(max(i["rnorm_true"] / i["bnorm"] for i in infos))}
+            "max_true_rel_residual": float(max(i["rnorm_true"] / i["bnorm"] for i in infos)),
+            "roofline": {"bound": "hbm", "achieved_gbs": achieved, "peak_gbs": hbm, "frac": achieved / hbm,
+                         "alg_bytes_per_unknown_iteration": bytes_it, "mean_unknowns": mean_n,
+                         "note": "algorithmic bytes of all system-iterations over the launch time"},
+            "restart_truncation": restart_trunc}
 
 
 def extra_config1(ctx, dev, args) -> dict:
@@ -710,6 +761,7 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo") -> di
     wall = time.perf_counter() - t0
     srv.close()
     lat = np.array([res[2] for res in results])
+    its = [int(res[1]["iterations"]) for res in results]
     unknowns = int(sum(r["side"] ** 3 for r in reqs))
     return {"workers": workers, "order": order, "requests": len(reqs),
             "converged": int(sum(res[1]["status_name"] == "ok" for res in results)),
@@ -717,7 +769,9 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo") -> di
             "solves_per_s": len(reqs) / wall, "unknowns_per_s": unknowns / wall,
             "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
             "max_latency_ms": float(lat.max()),
-            "max_true_rel_residual": float(max(res[1]["rnorm_true"] / res[1]["bnorm"] for res in results))}
+            "iterations_per_s": float(sum(its)) / wall,
+            "max_true_rel_residual": float(max(res[1]["rnorm_true"] / res[1]["bnorm"] for res in results)),
+            "_iterations": its}
 
 
 def extra_serve(ctx, dev, args) -> dict:
@@ -731,7 +785,38 @@ def extra_serve(ctx, dev, args) -> dict:
     out["workload"] = f"first {len(reqs)} requests of the seeded stream, replayed at their arrival times"
     # the same replay with the smallest queued request admitted first
     out["smallest_first"] = _serve_replay(ctx, reqs, probs, args.serve_workers, order="smallest_first")
+    out["oracle_per_request"] = oracle_request_sample(reqs, probs, out.pop("_iterations"))
+    out["smallest_first"].pop("_iterations", None)
     return out
+
+
+def oracle_request_sample(reqs, probs, iterations, count: int = 3) -> dict:
+    """The oracle on the `count` smallest requests of the replay: pipeline fill
+    plus two iterations timed on one host core, extrapolated to the GPU's
+    iteration count of that request."""
+    from oracle import krylov as K
+    from oracle import operators as O
+    from oracle import preconditioners as PC
+    meth = {0: "pipefcg", 1: "pipegcr", 2: "pipefgmres"}
+    order = sorted(range(len(reqs)), key=lambda j: reqs[j]["side"])[:count]
+    rows = []
+    for j in order:
+        r, c = reqs[j], probs[j]
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        m = meth[r["method"]]
+        prm0 = K.Params(mmax=30, rtol=1e-8, maxit=0, true_residual_check=False, sigma=1.0)
+        prm2 = K.Params(mmax=30, rtol=1e-8, maxit=2, true_residual_check=False, sigma=1.0)
+        t0 = time.perf_counter()
+        K.solve(m, aop, PC.InnerPCG(aop, 4), c["b"], prm=prm0)
+        t_fill = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        K.solve(m, aop, PC.InnerPCG(aop, 4), c["b"], prm=prm2)
+        t_it = max(time.perf_counter() - t0 - t_fill, 1e-9) / 2
+        its = int(iterations[j])
+        rows.append({"side": r["side"], "method": m, "gpu_iterations": its,
+                     "oracle_ms_extrapolated": 1e3 * (t_fill + its * t_it)})
+    return {"sample": f"the {count} smallest requests of the replay; oracle fill + 2 iterations on one core, "
+                      "extrapolated to the GPU's iteration count", "requests": rows}
 
 
 def extra_serve_sweep(ctx, dev, args) -> dict:
@@ -748,6 +833,8 @@ def extra_serve_sweep(ctx, dev, args) -> dict:
         scale = 1.0 if rate is None else (len(reqs) / rate) / span
         runs.append(_serve_replay(ctx, reqs, probs, 8, scale))
     runs.append(_serve_replay(ctx, reqs, probs, 1, 1.0))
+    for r in runs:
+        r.pop("_iterations", None)
     return {"workload": "first 16 requests of the seeded stream at several offered rates", "runs": runs}
 
 

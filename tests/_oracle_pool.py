@@ -17,7 +17,11 @@ import os
 import sys
 from concurrent.futures import ProcessPoolExecutor
 
-import numpy as np
+# one BLAS thread per worker process (set before numpy loads its BLAS)
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

@@ -139,13 +139,17 @@ def _csr_arrays(c):
 
 
 def test_smallest_first_order(ctx):
-    """PFK_SERVE_SMALLEST_FIRST with a budget below any request's estimate:
-    one request at a time; the first one admitted starts while the others are
-    still being queued, the rest run by increasing size; every result equals
-    the request solved alone."""
+    """PFK_SERVE_SMALLEST_FIRST with one worker and a budget below any
+    request's estimate: one solve at a time, so completion order is admission
+    order.  The largest request is submitted first (it is admitted at once and
+    its solve outlasts the submission of the others); the rest must then run by
+    increasing size (equal sizes by arrival).  Every result equals the request
+    solved alone."""
     from paper_1511_07226_gb300 import pfk
     reqs = _requests(6, 14, 30)
-    srv = pfk.Server(ctx, workers=4, memory_budget=1, order="smallest_first")
+    big = W.request_problem(dict(side=40, log_contrast=4.0, method=0, item_id=777), ell=4.0)
+    reqs = [(dict(side=40, method=0), big)] + reqs
+    srv = pfk.Server(ctx, workers=1, memory_budget=1, order="smallest_first")
     t0, tickets = [], []
     for r, c in reqs:
         t0.append(time.perf_counter())
@@ -153,13 +157,9 @@ def test_smallest_first_order(ctx):
     results = [srv.poll(t) for t in tickets]
     srv.close()
     done = [ts + lat / 1e3 for ts, (_, _, lat) in zip(t0, results)]
-    first = int(np.argmin(done))
-    rest = sorted((j for j in range(len(reqs)) if j != first), key=lambda j: (reqs[j][0]["side"], j))
-    # after the first admitted request (admitted before the others arrived),
-    # completions follow the size order (equal sizes by arrival), up to clock
-    # jitter
-    order = [done[j] for j in rest]
-    assert all(b >= a - 2e-3 for a, b in zip(order, order[1:])), (rest, np.diff(order))
+    completion = sorted(range(len(reqs)), key=lambda j: done[j])
+    expected = [0] + sorted(range(1, len(reqs)), key=lambda j: (reqs[j][0]["side"], j))
+    assert completion == expected, (completion, expected)
     for (r, c), (x, info, _) in zip(reqs, results):
         xa, ia = _alone(ctx, c, METHOD_OF[r["method"]])
         assert info["status_name"] == ia["status_name"] == "ok"
@@ -167,6 +167,46 @@ def test_smallest_first_order(ctx):
 
 
 def test_unknown_order_rejected(ctx):
+    """An admission order the library does not know: PFK_ERR_INVALID from
+    pfk_server_create itself (raw call), and the binding's name lookup."""
+    import ctypes as C
     from paper_1511_07226_gb300 import pfk
+    lib = pfk.load()
+    p = pfk.ServerParams()
+    p.workers, p.order = 1, 2
+    h = C.c_void_p()
+    assert lib.pfk_server_create(ctx.h, C.byref(p), C.byref(h)) == -1   # PFK_ERR_INVALID
+    assert not h.value
     with pytest.raises(KeyError):
         pfk.Server(ctx, order="largest_first")
+
+
+@pytest.mark.parametrize("method", ["pipefcg", "pipegcr", "pipefgmres"])
+def test_served_results_match_oracle(ctx, method):
+    """Served solves (4 workers, several requests in flight) against the oracle
+    with the protocol of tests/_parity.py: a request of each method on the
+    stream's field, contrast 1e2 (small sides), histories from a served run of
+    the same request on a fresh server."""
+    from oracle import krylov as K
+    from oracle import preconditioners as PC
+    from paper_1511_07226_gb300 import pfk
+    from tests._parity import check_solve, oracle_with_envelope
+    reqs = _requests(4, 14, 20)
+    c = W.request_problem(dict(side=16, log_contrast=2.0, method=0, item_id=4242), ell=4.0)
+    srv = pfk.Server(ctx, workers=4)
+    others = [srv.submit(cc["dims"], cc["eta"], cc["b"], method=METHOD_OF[r["method"]], **KW) for r, cc in reqs]
+    t = srv.submit(c["dims"], c["eta"], c["b"], method=method, sigma=1.0, **KW)
+    x, info, _ = srv.poll(t)
+    for o in others:
+        srv.poll(o)
+    srv.close()
+    # the served history is that of the same solve alone (bitwise, tested
+    # above); the alone run provides it
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
+    xa, ia, hist = pfk.solve(ctx, op, pc, c["b"], method=method, sigma=1.0, history=4000, **KW)
+    assert np.array_equal(x, xa) and info["iterations"] == ia["iterations"]
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    prm = K.Params(mmax=30, rtol=1e-8, maxit=3000, sigma=1.0)
+    ref, alts = oracle_with_envelope(method, aop, lambda: PC.InnerPCG(aop, 4), c["b"], prm)
+    check_solve(hist, ia, ref, alts, rtol=1e-8)
