@@ -50,11 +50,11 @@ WORKLOAD = "PIPEFCG nu_max=30, 3D 128^3 variable-coefficient Poisson (contrast 1
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic per launch of the fused pass from the committed ncu summary
-# (profiles/pipefcg_pass_96cube.md): one full-window launch (nu = 30) on 96^3,
-# 948.19 MB read + written against 955.51 MB algorithmic, scaled to 128^3 by
+# (profiles/pipefcg_pass_96cube.md): full-window launches (nu = 30) on 96^3,
+# 946.5 MB read + written against 955.5 MB algorithmic, scaled to 128^3 by
 # the number of unknowns.  Valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha256": "5af4459eb296c1b8cb5a1ff81813fd76f01c18899f00dc678f2903cd6a67ae4f",
-               "bytes_per_launch": 2.2478e9, "alg_bytes_per_launch": 2.2649e9, "window": 30,
+NCU_TRAFFIC = {"source_sha256": "1955fd3bb31558d06c256f6ab35c20380e124baf585e622e300845d001cc469a",
+               "bytes_per_launch": 2.2436e+09, "alg_bytes_per_launch": 2.2649e+09, "window": 30,
                "captured_on": "96^3, scaled by 128^3/96^3"}
 
 
@@ -787,7 +787,30 @@ def extra_serve(ctx, dev, args) -> dict:
     out["smallest_first"] = _serve_replay(ctx, reqs, probs, args.serve_workers, order="smallest_first")
     out["oracle_per_request"] = oracle_request_sample(reqs, probs, out.pop("_iterations"))
     out["smallest_first"].pop("_iterations", None)
+    out["one_cta_vs_whole_gpu"] = one_cta_vs_whole_gpu(ctx)
     return out
+
+
+def one_cta_vs_whole_gpu(ctx) -> dict:
+    """Why served requests run the whole-GPU path: the time per PIPEFCG
+    iteration of one small 3D request (4 inner FP64 PCG iterations) in the
+    persistent batched kernel (one CTA owns the system) against the whole-GPU
+    graph path, at 100 iterations each."""
+    import workloads as W
+    from paper_1511_07226_gb300 import pfk
+    rows = []
+    for side in (24, 32, 48):
+        p = W.poisson3d_gaussian(n=side, ell=4.0, log_contrast=2.0, config_id=5, item_id=800 + side)
+        op = pfk.Operator.stencil(ctx, p["dims"], p["eta"])
+        kw = dict(mmax=30, rtol=1e-300, maxit=100, max_restarts=0)
+        pfk.solve_batched(ctx, [op], [p["b"]], pc_kind="inner_pcg", inner_iters=4, precision="fp64", **kw)
+        _, bi, _ = pfk.solve_batched(ctx, [op], [p["b"]], pc_kind="inner_pcg", inner_iters=4, precision="fp64", **kw)
+        pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
+        pfk.solve(ctx, op, pc, p["b"], **kw)
+        _, gi, _ = pfk.solve(ctx, op, pc, p["b"], **kw)
+        rows.append({"side": side, "one_cta_ms_per_iteration": bi[0]["time_ms"] / max(bi[0]["iterations"], 1),
+                     "whole_gpu_ms_per_iteration": gi["time_ms"] / max(gi["iterations"], 1)})
+    return {"note": "PIPEFCG nu_max=30, 4 inner FP64 Jacobi-PCG, 100 iterations each", "runs": rows}
 
 
 def oracle_request_sample(reqs, probs, iterations, count: int = 3) -> dict:

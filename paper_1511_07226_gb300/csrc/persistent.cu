@@ -154,16 +154,26 @@ __device__ __forceinline__ void wait_partials() {
 }
 
 // Sums the fetched rows s_part[b * kPerNd + j], b < nb, j < nd, in a fixed
-// order (lane l of warp w: rows l, l + 32, ... of columns w, w + 4, ..., then a
-// fixed shuffle tree) into out[j] (shared memory).  Every block that calls it
-// gets bitwise the same sums.
-__device__ __forceinline__ void sum_partials(const double* s_part, int nb, int nd, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = warp; j < nd; j += kPerThreads / 32) {
+// order into out[j] (shared memory).  Each FP64 instruction costs a
+// sub-partition tens of nanoseconds whatever its lane count, so the work is
+// spread over (column, row group) tasks that keep all lanes busy: task t of
+// the block sums rows g, g + G, g + 2G, ... of column j (t = g * nd + j, G =
+// the groups that fit in the block's threads, at most 4), then thread j adds
+// the G group sums in group order.  Every block gets bitwise the same sums.
+__device__ __forceinline__ void sum_partials(const double* s_part, int nb, int nd, double* out, double* s_grp) {
+  int G = kPerThreads / nd;
+  G = G < 1 ? 1 : (G > 4 ? 4 : G);
+  for (int t = threadIdx.x; t < G * nd; t += kPerThreads) {
+    const int g = t / nd, j = t - g * nd;
     double a = 0.0;
-    for (int b = lane; b < nb; b += 32) a += s_part[b * kPerNd + j];
-    a = warp_sum(a);
-    if (lane == 0) out[j] = a;
+    for (int b = g; b < nb; b += G) a += s_part[b * kPerNd + j];
+    s_grp[t] = a;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nd; j += kPerThreads) {
+    double a = s_grp[j];
+    for (int g = 1; g < G; ++g) a += s_grp[g * nd + j];
+    out[j] = a;
   }
   __syncthreads();
 }
@@ -555,7 +565,7 @@ __global__ void __launch_bounds__(kPerThreads) pipefcg_persistent(PersistArgs a)
       if (e >= 0 && q == 0) sn[l] = csr_row(a, cs, mnew, e, l);
     }
     wait_partials();
-    sum_partials(s_part, nb, 4 + nwp, st.sums);
+    sum_partials(s_part, nb, 4 + nwp, st.sums, s_red);
 
     // ---- scalar phase of iteration i (Alg. 8), the same in every block ----
     // Warp 1 (thread 32) forms rho_i and the convergence verdict and writes the
@@ -712,7 +722,7 @@ __global__ void __launch_bounds__(kPerThreads) fcg_persistent(PersistArgs a) {
     }
     fetch_partials(red1, nb, s_part);
     wait_partials();
-    sum_partials(s_part, nb, 4 + nu, st.sums);
+    sum_partials(s_part, nb, 4 + nu, st.sums, s_red);
     // Alg. 2: gamma_i, convergence (thread 32), beta_{i,k} = -<u_i, s_k> / eta_k
     // (warp 0, used only when the iteration goes on)
     if (threadIdx.x == 32) {
@@ -785,7 +795,7 @@ __global__ void __launch_bounds__(kPerThreads) fcg_persistent(PersistArgs a) {
     }
     fetch_partials(red3, nb, s_part);
     wait_partials();
-    sum_partials(s_part, nb, 1, st.sums);
+    sum_partials(s_part, nb, 1, st.sums, s_red);
     if (threadIdx.x == 0) {
       // Alg. 2: eta_i = <p_i, s_i>, alpha_i = gamma_i / eta_i
       const double eta = st.sums[0];
