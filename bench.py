@@ -439,6 +439,27 @@ def main():
                  "reference_solution": f"FP64 FCG (Alg. 2) on the GPU to rtol 1e-11 "
                                        f"({iref['iterations']} iterations, true rel residual "
                                        f"{iref['rnorm_true'] / iref['bnorm']:.2e})"}
+        # the same with BF16-stored operator coefficients in the FP32 inner PCG
+        pc16 = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4, precision="bf16")
+        x.zero_()
+        pfk.solve(ctx, op, pc16, b, x0=x, **kw)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        binfo = []
+        b0.record(stream)
+        for _ in range(args.mixed_steps):
+            x.zero_()
+            xb, bi, _ = pfk.solve(ctx, op, pc16, b, x0=x, **kw)
+            binfo.append(bi)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        bms = b0.elapsed_time(b1) / args.mixed_steps
+        bits = int(np.median([i["iterations"] for i in binfo]))
+        mixed["bf16_coefficients"] = {
+            "time_to_1e-8_ms": bms, "iterations": bits, "ms_per_iteration": bms / max(bits, 1),
+            "true_rel_residual": binfo[-1]["rnorm_true"] / binfo[-1]["bnorm"], "speedup_vs_fp64": ms_max / bms,
+            "rel_error_vs_fp64_solve": float(torch.linalg.vector_norm(xb - x64) / torch.linalg.vector_norm(x64)),
+            "rel_error_vs_reference": float(torch.linalg.vector_norm(xb - xref)) / nref}
 
     extras = {}
     wanted = [e for e in args.extras.split(",") if e and e != "none"]
