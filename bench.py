@@ -73,6 +73,21 @@ def replica_value(world: int, ms_max: float) -> float:
     return world * 1e3 / ms_max
 
 
+def iteration_roofline(pass_flops: float, n: int, ms_per_iteration: float, probe_tflops: float) -> dict:
+    """FP64 work of a whole PIPEFCG iteration against the FP64 peaks: the fused
+    pass's flops (the library's count, average window) plus, per unknown, the
+    preconditioner's (4 inner Jacobi-PCG iterations: first step 2 FP64
+    operations, s = A p with <s, p> 8, r update with <D^-1 r, r> 3, x / p updates
+    3 for each of the 3 further iterations, final x 2: 54) and the operator's
+    n = A m (7), each operation an FMA-sized instruction (2 flops)."""
+    flops = pass_flops + 2.0 * (54 + 7) * n
+    achieved = flops / (ms_per_iteration * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+            "frac": achieved / FP64_PEAK_TFLOPS, "measured_fp64_rate": probe_tflops,
+            "frac_of_measured_rate": achieved / probe_tflops, "flops_per_iteration": flops,
+            "note": "whole iteration (pass + inner PCG + operator) over the time per iteration of the timed solves"}
+
+
 def peak_hbm_gbs() -> float:
     return float(measured_peaks().get("hbm_gbs", 6800.0))
 
@@ -495,6 +510,7 @@ def main():
                      "alg_bytes_per_pass": pass_bytes, "alg_flops_per_pass": pass_flops,
                      "passes": pinfo["pass_launches"]},
         "gpu_launches": launches,
+        "iteration_roofline": iteration_roofline(pass_flops, n, ms_max / max(its, 1), fp64_probe["tflops"]),
         "mixed_fp32_pc": mixed,
         **extras,
         "cpu_baseline": cpu,

@@ -100,3 +100,37 @@ def test_two_phase_pipefgmres_chebyshev_10_iterations(ctx, oracle_jobs):
     s = check_solve(hist, info, ref, alts)
     assert s["prefix"] >= 10, s
     assert np.all(np.isfinite(hist[:, 0]))
+
+
+def _spreads():
+    import glob
+    import json
+    import os
+    out = []
+    for f in sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "oracle_spread_*cube.json"))):
+        with open(f) as fh:
+            out.append(json.load(fh))
+    return out
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("doc", _spreads(), ids=lambda d: f"{d['method']}-{d['problem']['kw']['n']}")
+def test_iteration_count_within_oracle_spread(ctx, doc):
+    """The GPU's whole solve in the headline regime takes a number of
+    iterations inside the range of the oracle's own runs under other
+    roundings (tests/golden/oracle_spread_*.json, written by
+    tests/golden/make_oracle_spread.py), widened by half that range on each
+    side: with this preconditioner the count is decided by when the
+    residual-replacement restarts fire, which rounding alone moves."""
+    from tests import _oracle_pool as P
+    c = P.problem(doc["problem"])
+    if P.input_hash(c) != doc["inputs_sha256"]:
+        pytest.skip("inputs differ from the stored spread's")
+    its = [r["iterations"] for r in doc["runs"] if r["status"] == "converged"]
+    assert len(its) == len(doc["runs"]), doc["runs"]
+    x, info, _ = _gpu_solve(ctx, c, doc["method"], "inner_pcg", 4, 0, rtol=doc["prm"]["rtol"],
+                            maxit=doc["prm"]["maxit"], max_restarts=doc["prm"]["max_restarts"])
+    lo, hi = min(its), max(its)
+    half = 0.5 * (hi - lo) + 2
+    assert info["status_name"] == "ok" and info["rnorm_true"] <= doc["prm"]["rtol"] * info["bnorm"]
+    assert lo - half <= info["iterations"] <= hi + half, (info["iterations"], its)
