@@ -124,10 +124,9 @@ __device__ __forceinline__ bool grid_barrier(SolveCtl* ctl) {
   return s_ok != 0;
 }
 
-// Sum over the 32 rows of a chunk of a value held by thread q = j % 4 of each
-// row (lanes q, q + 4, ..., q + 28 of a warp), then over the block's four
-// warps in order: red[j] for j < nd.  `v` is this thread's value of column
-// (4 * slot + q); call with every thread.  smem: 4 * nd doubles.
+// Sum of a value over the eight rows a warp holds, for the thread position q
+// of a row: lanes q, q + 4, ..., q + 28 (a fixed shuffle tree; every lane gets
+// the sum of its own q).  Call with all 32 lanes.
 __device__ __forceinline__ double quad_col_sum(double v) {
   v += __shfl_xor_sync(0xffffffffu, v, 4);
   v += __shfl_xor_sync(0xffffffffu, v, 8);
