@@ -742,10 +742,10 @@ def extra_config1(ctx, dev, args) -> dict:
 
 def extra_fgmres256(ctx, dev, args) -> dict:
     """PIPEFGMRES (Alg. 15) restart 30 on 256^3 two-phase advection-diffusion:
-    8 Chebyshev-Jacobi sweeps with BF16-stored coefficients / FP32 vectors against
-    FP64.  The one-level preconditioner leaves this problem far from 1e-8 within
-    a few thousand iterations, so a fixed iteration budget is timed and the
-    residual reached is reported."""
+    8 Chebyshev-Jacobi sweeps with BF16-stored coefficients / FP32 vectors (and
+    FP32 coefficients / vectors) against FP64.  The one-level preconditioner
+    leaves this problem far from 1e-8 within thousands of iterations, so each
+    arm is timed to a common relative residual (true residual checked)."""
     import torch
     import workloads as W
     from paper_1511_07226_gb300 import pfk
@@ -757,7 +757,7 @@ def extra_fgmres256(ctx, dev, args) -> dict:
                        f"(true residual checked), at most {FGMRES256_ITERS} iterations",
            "n_unknowns": int(b.numel()), "rtol": FGMRES256_RTOL}
     xs = {}
-    for prec in ("bf16", "fp64"):
+    for prec in ("bf16", "fp32", "fp64"):
         pc = pfk.Preconditioner(ctx, op, "chebyshev", inner_iters=8, precision=prec)
         x = torch.zeros_like(b)
         xo, info, _ = pfk.solve(ctx, op, pc, b, x0=x, method="pipefgmres", mmax=30, rtol=FGMRES256_RTOL,
@@ -770,6 +770,9 @@ def extra_fgmres256(ctx, dev, args) -> dict:
     out["speedup_per_iteration_bf16_vs_fp64"] = out["fp64"]["ms_per_iteration"] / out["bf16"]["ms_per_iteration"]
     out["speedup_time_to_rtol_bf16_vs_fp64"] = out["fp64"]["time_to_rtol_ms"] / out["bf16"]["time_to_rtol_ms"]
     out["bf16_rel_error_vs_fp64_solve"] = float(torch.linalg.vector_norm(xs["bf16"] - xs["fp64"]) /
+                                                torch.linalg.vector_norm(xs["fp64"]))
+    out["speedup_time_to_rtol_fp32_vs_fp64"] = out["fp64"]["time_to_rtol_ms"] / out["fp32"]["time_to_rtol_ms"]
+    out["fp32_rel_error_vs_fp64_solve"] = float(torch.linalg.vector_norm(xs["fp32"] - xs["fp64"]) /
                                                 torch.linalg.vector_norm(xs["fp64"]))
     return out
 
