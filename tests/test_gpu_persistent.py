@@ -142,3 +142,31 @@ def test_bitwise_reproducible(ctx, method):
     assert np.array_equal(x1, x2) and np.array_equal(h1, h2, equal_nan=True)
     assert np.array_equal(x1, x3) and i3["iterations"] == i1["iterations"]
     assert i1["status_name"] == "ok"
+
+
+@pytest.mark.parametrize("method", ["pipefcg", "fcg"])
+def test_general_csr_jacobi_nonzero_initial_guess(ctx, method):
+    """A general CSR operator (random, diagonally dominant, symmetrised) with
+    Jacobi and a nonzero x_0: r_0 = b - A x_0 in the fill, D^-1 from the CSR
+    diagonal."""
+    from paper_1511_07226_gb300 import pfk
+    rp, ci, va = W.random_csr(3000, per_row=6, item_id=31)
+    a = np.zeros((3000, 3000))
+    rows = np.repeat(np.arange(3000), np.diff(rp))
+    a[rows, ci] = va
+    a = 0.5 * (a + a.T)
+    nz = np.nonzero(a)
+    order = np.lexsort((nz[1], nz[0]))
+    r_, c_ = nz[0][order], nz[1][order]
+    rp2 = np.concatenate([[0], np.cumsum(np.bincount(r_, minlength=3000))]).astype(np.int32)
+    ci2 = c_.astype(np.int32)
+    va2 = a[r_, c_]
+    aop = O.CsrOperator(rp2, ci2, va2)
+    b = W.random_vector(3000, 32)
+    x0 = 0.1 * W.random_vector(3000, 33)
+    prm = K.Params(mmax=30, rtol=1e-9, maxit=2000)
+    ref, alts = oracle_with_envelope(method, aop, lambda: PC.JacobiPC(aop), b, prm, x0=x0)
+    op = pfk.Operator.csr(ctx, rp2, ci2, va2)
+    x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), b, x0=x0, method=method, mmax=30,
+                              rtol=1e-9, maxit=2000, history=2100, persistent="on")
+    check_solve(hist, info, ref, alts, rtol=1e-9)
