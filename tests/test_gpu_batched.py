@@ -124,3 +124,20 @@ def test_batched_nonzero_initial_guess(ctx):
         ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.JacobiPC(aop), c["b"],
                                          K.Params(mmax=20, rtol=1e-8, maxit=1000), x0=x0)
         check_solve(h, info, ref, alts, rtol=1e-8)
+
+
+def test_batched_restart_truncation(ctx):
+    """Restart-style truncation (Sec. 5 remark, nu_i = ((i - 1) mod nu_max) + 1)
+    in the batched kernel against the oracle, inner FP64 PCG."""
+    from paper_1511_07226_gb300 import pfk
+    sys_ = _systems([36, 28, 50])
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys_]
+    xs, infos, hists = pfk.solve_batched(ctx, ops, [c["b"] for c in sys_], pc_kind="inner_pcg", inner_iters=4,
+                                         precision="fp64", history=2000, block_threads=256, mmax=20,
+                                         truncation="restart", rtol=1e-8, maxit=1000, max_restarts=50)
+    for c, info, h in zip(sys_, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.InnerPCG(aop, 4), c["b"],
+                                         K.Params(mmax=20, rtol=1e-8, maxit=1000, truncation="restart",
+                                                  max_restarts=50))
+        check_solve(h, info, ref, alts, rtol=1e-8)
