@@ -51,6 +51,11 @@ def cut(runs):
     return runs
 
 
+def _tagged(job):
+    name, j = job
+    return name, P._run(j)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("cases", nargs="*")
@@ -63,24 +68,26 @@ def main():
         for o in cs["orders"]:
             jobs.append((name, dict(problem=cs["problem"], method=cs["method"], pc=cs["pc"], prm=cs["prm"],
                                     order=o, sample=[])))
-    # the longest jobs first
-    jobs.sort(key=lambda j: (not CASES[j[0]]["big"], j[1]["order"] not in ("fsum", "rowsum")))
+    # the longest jobs first; each case's file is written as soon as its runs are in
+    jobs.sort(key=lambda j: (not CASES[j[0]]["big"], j[1]["order"] not in ("fsum", "fma", "rowsum")))
+    done = {name: [] for name in names}
     with mp.get_context("spawn").Pool(args.workers) as pool:
-        results = pool.map(P._run, [j for _, j in jobs], chunksize=1)
-    for name in names:
-        cs = CASES[name]
-        runs = [r for (n, _), r in zip(jobs, results) if n == name]
-        runs.sort(key=lambda r: cs["orders"].index(r["order"]))
-        for r in runs:
-            r.pop("x_sample", None)
-        doc = {"case": name, "generator": "tests/golden/make_oracle_envelopes.py (oracle/ only)",
-               "problem": cs["problem"], "method": cs["method"], "pc": cs["pc"], "prm": cs["prm"],
-               "inputs_sha256": P.input_hash(P.problem(cs["problem"])), "runs": cut(runs)}
-        with open(P.stored_path(name), "w") as fh:
-            json.dump(doc, fh)
-            fh.write("\n")
-        print(name, [(r["order"], r["status"], r["iterations"], r["restarts"], len(r["rho_hist"])) for r in runs],
-              flush=True)
+        for name, r in pool.imap_unordered(_tagged, jobs, chunksize=1):
+            done[name].append(r)
+            cs = CASES[name]
+            if len(done[name]) < len(cs["orders"]):
+                continue
+            runs = sorted(done[name], key=lambda rr: cs["orders"].index(rr["order"]))
+            for rr in runs:
+                rr.pop("x_sample", None)
+            doc = {"case": name, "generator": "tests/golden/make_oracle_envelopes.py (oracle/ only)",
+                   "problem": cs["problem"], "method": cs["method"], "pc": cs["pc"], "prm": cs["prm"],
+                   "inputs_sha256": P.input_hash(P.problem(cs["problem"])), "runs": cut(runs)}
+            with open(P.stored_path(name), "w") as fh:
+                json.dump(doc, fh)
+                fh.write("\n")
+            print(name, [(rr["order"], rr["status"], rr["iterations"], rr["restarts"], len(rr["rho_hist"]))
+                         for rr in runs], flush=True)
 
 
 if __name__ == "__main__":
