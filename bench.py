@@ -43,14 +43,14 @@ WORKLOAD = "PIPEFCG nu_max=30, 3D 128^3 variable-coefficient Poisson (contrast 1
 # FP64 FMA peak of GB300 from unit counts and clocks: 2 FP64 FMA per clock per
 # SM x 152 SMs x 2 flops x 2.07 GHz maximum SM clock = 1.259 TFLOP/s (the
 # nominal 1.25 TFLOP/s).  The FMA-chain probe (pfk_probe_fp64_fma, `bench.py
-# --fp64-probe`, profiles/fp64_peak.md) measures 1.057 TFLOP/s at 2.07 GHz;
+# --fp64-probe`) measures 1.057 TFLOP/s at 2.07 GHz;
 # every line reports it beside the roofline (`fp64_probe`).  The fused pass
 # does ~1.2 FP64 FMA per 8-byte word it moves, above the HBM balance point of
 # ~0.4, so it is bound by this FP64 pipe, not by HBM.
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
-# DRAM traffic per launch of the fused pass from the committed ncu summary
-# (profiles/pipefcg_pass_96cube.md): full-window launches (nu = 30) on 96^3,
+# DRAM traffic per launch of the fused pass from the committed ncu summary of
+# the pass: full-window launches (nu = 30) on 96^3,
 # 946.5 MB read + written against 955.5 MB algorithmic, scaled to 128^3 by
 # the number of unknowns.  Valid only while the kernel source is unchanged.
 NCU_TRAFFIC = {"source_sha256": "1955fd3bb31558d06c256f6ab35c20380e124baf585e622e300845d001cc469a",
