@@ -268,9 +268,13 @@ pfk_status pfk_pc_apply(pfk_context* ctx, const pfk_pc* pc, const double* v, dou
  *              bounded grid barriers (one per PIPEFCG iteration, three per FCG
  *              iteration) instead of kernel boundaries.  0 (default): when
  *              eligible; 1: never; 2: required (PFK_ERR_INVALID when not
- *              eligible).  A barrier wait that gives up (2 s) ends the solve
- *              with PFK_ERR_TIMEOUT.
- *  reserved    0. */
+ *              eligible).  A barrier wait that gives up (barrier_timeout_us)
+ *              ends the solve with PFK_ERR_TIMEOUT.
+ *  barrier_timeout_us  bound of each grid-barrier wait of the persistent
+ *              path: 0 = 2 s; > 0 = that many microseconds; < 0 = no wait
+ *              allowed (a barrier that has to wait fails at once: the solve
+ *              ends with PFK_ERR_TIMEOUT and the context stays usable -- for
+ *              testing the time-out path). */
 typedef struct {
   int32_t method;
   int32_t mmax;
@@ -287,7 +291,7 @@ typedef struct {
   int32_t history_capacity;
   int32_t profile;
   int32_t persistent;
-  int32_t reserved;
+  int32_t barrier_timeout_us;
 } pfk_solve_params;
 
 typedef struct {

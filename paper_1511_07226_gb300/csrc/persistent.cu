@@ -41,7 +41,6 @@ namespace pfk {
 constexpr int kPerThreads = 128;
 constexpr int kPerRows = 32;                // rows of a chunk (4 threads per row)
 constexpr int kPerNd = PFK_MAX_MMAX + 4;    // largest partial row (gamma, delta, ||r||^2, c_{i-1}, window)
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 constexpr int kMaxPerBlocks = 192;          // grid cap (the partial rows live in shared memory: 54 KB)
 constexpr int kPerSmemLimit = 220 * 1024;   // dynamic shared memory of one block (of 227 KB)
 
@@ -95,8 +94,9 @@ __device__ __forceinline__ void red_add_release(unsigned int* p, unsigned int v)
 // counter (acquire-release: the block's writes, ordered before thread 0 by the
 // block barrier, are released; the last arrival acquires everyone's); the last
 // arrival resets the counter and bumps the generation with a release, the
-// others wait for it with acquire loads.  The wait is bounded: on time-out the
-// block raises bar_abort, and a raised bar_abort ends every other wait.
+// others wait for it with acquire loads.  The wait is bounded (the control
+// block's bar_timeout_ns, 2 s by default): on time-out the block raises
+// bar_abort, and a raised bar_abort ends every other wait.
 // Returns false in that case.
 __device__ __forceinline__ bool grid_barrier(SolveCtl* ctl) {
   __shared__ int s_ok;
@@ -109,9 +109,10 @@ __device__ __forceinline__ bool grid_barrier(SolveCtl* ctl) {
       red_add_release(&ctl->bar_gen, 1u);
     } else {
       const unsigned long long t0 = global_ns();
+      const long long budget = ctl->bar_timeout_ns;
       while (ld_acquire(&ctl->bar_gen) == g) {
         if (ld_acquire(&ctl->bar_abort)) { ok = 0; break; }
-        if (global_ns() - t0 > kBarrierTimeoutNs) {
+        if (budget <= 0 || global_ns() - t0 > (unsigned long long)budget) {
           atomicExch(&ctl->bar_abort, 1u);
           ok = 0;
           break;

@@ -71,6 +71,7 @@ struct SolveCtl {
   unsigned int bar_gen;    // generation (bumped by the last arrival),
   unsigned int bar_abort;  // set when a wait timed out (every block then leaves)
   unsigned int bar_pad;
+  long long bar_timeout_ns;  // bound of each barrier wait (<= 0: no wait allowed)
 };
 
 // Control block of a preconditioner application (inner iterations).

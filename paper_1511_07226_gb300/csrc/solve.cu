@@ -195,6 +195,8 @@ pfk_status run_solve(pfk_context* ctx, const pfk_operator* op, const pfk_pc* pc,
   h.atol = prm->atol;
   h.history = hist;
   h.hist_cap = hist_cap;
+  h.bar_timeout_ns = prm->barrier_timeout_us == 0 ? 2000000000ll
+                     : prm->barrier_timeout_us < 0 ? 0ll : 1000ll * (long long)prm->barrier_timeout_us;
   PFK_CUDA(ctx, cudaMemcpyAsync(ctl, &h, sizeof(SolveCtl), cudaMemcpyHostToDevice, st));
 
   SolveEnv env;

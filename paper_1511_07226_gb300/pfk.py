@@ -50,7 +50,7 @@ class SolveParams(C.Structure):
                 ("rtol", C.c_double), ("atol", C.c_double), ("maxit", C.c_int32), ("max_restarts", C.c_int32),
                 ("sigma", C.c_double), ("true_residual_check", C.c_int32), ("graph_iters", C.c_int32),
                 ("history", C.c_void_p), ("history_capacity", C.c_int32), ("profile", C.c_int32),
-                ("persistent", C.c_int32), ("reserved", C.c_int32)]
+                ("persistent", C.c_int32), ("barrier_timeout_us", C.c_int32)]
 
 
 class InnerSolve(C.Structure):
@@ -342,7 +342,7 @@ def default_params() -> SolveParams:
 
 def make_params(method="pipefcg", mmax=30, truncation="standard", norm="natural", rtol=1e-8, atol=0.0,
                 maxit=10000, max_restarts=20, sigma=float("nan"), true_residual_check=True,
-                graph_iters=8, profile=False, persistent="auto") -> SolveParams:
+                graph_iters=8, profile=False, persistent="auto", barrier_timeout_us=0) -> SolveParams:
     p = default_params()
     p.method = METHODS[method]
     p.mmax = int(mmax)
@@ -355,6 +355,7 @@ def make_params(method="pipefcg", mmax=30, truncation="standard", norm="natural"
     p.graph_iters = int(graph_iters)
     p.profile = 1 if profile else 0
     p.persistent = PERSISTENT[persistent]
+    p.barrier_timeout_us = int(barrier_timeout_us)
     return p
 
 

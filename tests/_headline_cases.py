@@ -19,8 +19,11 @@ def field(n: int) -> dict:
 CASES = {}
 for _m in ("pipefcg", "pipegcr"):
     for _n in (32, 48):
+        # iteration cap 5000: a rounding that makes the solve stagnate ends
+        # there ("maxit"), and the outcome is then not compared (the
+        # alternative runs disagree on it)
         CASES[f"{_m}_{_n}"] = dict(problem=field(_n), method=_m, pc=("inner_pcg", {"k": 4}),
-                                   prm=dict(mmax=30, rtol=1e-8, maxit=20000, max_restarts=200),
+                                   prm=dict(mmax=30, rtol=1e-8, maxit=5000, max_restarts=200),
                                    orders=ALL_ORDERS, big=False)
     CASES[f"{_m}_128_first100"] = dict(problem={"gen": "poisson3d_gaussian", "kw": {"n": 128}}, method=_m,
                                        pc=("inner_pcg", {"k": 4}), prm=dict(mmax=30, rtol=1e-8, maxit=100),

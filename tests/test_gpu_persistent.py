@@ -170,3 +170,23 @@ def test_general_csr_jacobi_nonzero_initial_guess(ctx, method):
     x, info, hist = pfk.solve(ctx, op, pfk.Preconditioner(ctx, op, "jacobi"), b, x0=x0, method=method, mmax=30,
                               rtol=1e-9, maxit=2000, history=2100, persistent="on")
     check_solve(hist, info, ref, alts, rtol=1e-9)
+
+
+@pytest.mark.parametrize("method", ["pipefcg", "fcg"])
+def test_barrier_timeout_reported_and_context_usable(ctx, method):
+    """Failure detection without a GPU fault: with no barrier wait allowed
+    (barrier_timeout_us < 0), the first barrier that has to wait gives up, every
+    block leaves, and the solve returns PFK_ERR_TIMEOUT; the context then solves
+    the same problem normally, bitwise as before."""
+    from paper_1511_07226_gb300 import pfk
+    c, _ = _csr_problem((64, 64))
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"], storage="csr")
+    pc = pfk.Preconditioner(ctx, op, "jacobi")
+    kw = dict(method=method, mmax=30, rtol=1e-8, persistent="on")
+    x0, i0, _ = pfk.solve(ctx, op, pc, c["b"], **kw)
+    with pytest.raises(pfk.PfkError, match="timed out") as err:
+        pfk.solve(ctx, op, pc, c["b"], barrier_timeout_us=-1, **kw)
+    assert err.value.status == -6   # PFK_ERR_TIMEOUT
+    x1, i1, _ = pfk.solve(ctx, op, pc, c["b"], **kw)
+    assert i1["status_name"] == "ok" and i1["iterations"] == i0["iterations"]
+    assert np.array_equal(x1, x0)
