@@ -802,6 +802,7 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo") -> di
     srv.close()
     lat = np.array([res[2] for res in results])
     its = [int(res[1]["iterations"]) for res in results]
+    unk_its = float(sum(int(np.prod(p["dims"])) * i for p, i in zip(probs, its)))
     unknowns = int(sum(r["side"] ** 3 for r in reqs))
     return {"workers": workers, "order": order, "requests": len(reqs),
             "converged": int(sum(res[1]["status_name"] == "ok" for res in results)),
@@ -810,6 +811,7 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo") -> di
             "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
             "max_latency_ms": float(lat.max()),
             "iterations_per_s": float(sum(its)) / wall,
+            "unknown_iterations_per_s": unk_its / wall,
             "max_true_rel_residual": float(max(res[1]["rnorm_true"] / res[1]["bnorm"] for res in results)),
             "_iterations": its}
 
