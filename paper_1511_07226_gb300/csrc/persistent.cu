@@ -456,6 +456,7 @@ __global__ void __launch_bounds__(kPerThreads) pipefcg_persistent(PersistArgs a)
     cs.cap = L.csr_cap;
   }
   load_state(&st, ctl);
+  if (st.status != kRun) return;   // a launch queued behind the one that finished
   {
     double* gm = (st.i & 1) ? a.m1 : a.m0;
     double* gv[7] = {a.x, a.r, a.u, a.w, gm, a.n, const_cast<double*>(a.dinv)};
@@ -669,6 +670,7 @@ __global__ void __launch_bounds__(kPerThreads) fcg_persistent(PersistArgs a) {
   double* red1 = a.partials;                             // [nb][kPerNd]: gamma, ||r||^2, -, -, window dots
   double* red3 = a.partials + (size_t)nb * kPerNd;       // [nb][kPerNd]: eta
   load_state(&st, ctl);
+  if (st.status != kRun) return;   // a launch queued behind the one that finished
   {
     double* gv[4] = {a.x, a.r, a.u, const_cast<double*>(a.dinv)};
     double* gr[2] = {a.P, a.S};
