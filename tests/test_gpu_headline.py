@@ -23,7 +23,7 @@ import numpy as np
 import pytest
 
 from tests._headline_cases import CASES, SIGMA_256
-from tests._oracle_pool import envelope_runs
+from tests._oracle_pool import envelope_runs, load_stored
 from tests._parity import check_solve
 
 pytestmark = pytest.mark.gpu
@@ -32,17 +32,34 @@ SMALL = [("pipefcg", 32), ("pipefcg", 48), ("pipegcr", 32), ("pipegcr", 48)]
 FULL = ["pipefcg", "pipegcr"]
 
 
+class _Jobs:
+    """The module's oracle envelopes: the stored runs of
+    tests/golden/envelope_<case>.json when the inputs hash the same here,
+    otherwise submitted to the worker pool.  Cases without a stored file are
+    submitted together the first time any of them is needed (small cases
+    first), so their oracle runs overlap the GPU tests."""
+
+    def __init__(self):
+        self.jobs = {}
+
+    def _submit(self, name):
+        cs = CASES[name]
+        self.jobs[name] = envelope_runs(cs["problem"], cs["method"], cs["pc"], cs["prm"], orders=cs["orders"],
+                                        big=cs["big"], stored=name)
+
+    def __getitem__(self, name):
+        if name not in self.jobs:
+            self._submit(name)
+            if load_stored(name) is None:
+                for other in sorted(CASES, key=lambda k: CASES[k]["big"]):
+                    if other not in self.jobs and load_stored(other) is None:
+                        self._submit(other)
+        return self.jobs[name]
+
+
 @pytest.fixture(scope="module")
 def oracle_jobs():
-    """Every oracle envelope of the module: the stored runs of
-    tests/golden/envelope_<case>.json when the inputs hash the same here,
-    otherwise submitted to the worker pool at once (small cases first)."""
-    jobs = {}
-    for name in sorted(CASES, key=lambda k: CASES[k]["big"]):
-        cs = CASES[name]
-        jobs[name] = envelope_runs(cs["problem"], cs["method"], cs["pc"], cs["prm"], orders=cs["orders"],
-                                   big=cs["big"], stored=name)
-    return jobs
+    return _Jobs()
 
 
 @pytest.fixture(scope="module")
