@@ -29,8 +29,16 @@
 // split the direction window between them (k = q, q + 4, ... for thread q of
 // the row), so the four warps of a block spread the FP64 work over the SM's
 // four sub-partitions.  The quad sums are combined by a fixed shuffle tree, so
-// every run is bitwise reproducible.  Block 0 keeps the control block up to
-// date (status, counters, history) for the host driver.
+// every run is bitwise reproducible.  A block's rows of every vector and ring
+// slot, and its CSR rows, stay in shared memory for the whole launch (loaded
+// at the start, written back at the end); within a launch only m_i / p_i
+// (read by other blocks' operator rows) and the partial rows go through
+// global memory, the partial rows fetched with asynchronous 16-byte copies.
+// On this GPU an FP64 instruction costs its sub-partition tens of
+// nanoseconds whatever its active lanes, so the reductions and the scalar
+// phase are arranged to keep such instructions few and off one warp's chain.
+// Block 0 keeps the control block up to date (status, counters, history) for
+// the host driver.
 #include "pfk_internal.cuh"
 #include "solver.cuh"
 
@@ -41,7 +49,7 @@ namespace pfk {
 constexpr int kPerThreads = 128;
 constexpr int kPerRows = 32;                // rows of a chunk (4 threads per row)
 constexpr int kPerNd = PFK_MAX_MMAX + 4;    // largest partial row (gamma, delta, ||r||^2, c_{i-1}, window)
-constexpr int kMaxPerBlocks = 192;          // grid cap (the partial rows live in shared memory: 54 KB)
+constexpr int kMaxPerBlocks = 192;          // grid cap (the fetched partial rows take nb x 288 bytes)
 constexpr int kPerSmemLimit = 220 * 1024;   // dynamic shared memory of one block (of 227 KB)
 
 struct PersistArgs {
