@@ -371,22 +371,55 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
                              const pfk_solve_params* params, const double* const* b, double* const* x,
                              int ptrs_on_device, int block_threads, pfk_solve_info* infos);
 
+/* Solves nsys independent stencil systems with PIPEFCG (Alg. 8) on the
+ * grouped persistent kernel: each system is advanced by its own group of CTAs
+ * (a contiguous range of x-rows per CTA) and the active systems share
+ * cooperative launches of a few iterations each, between which finished
+ * systems leave and queued ones (in the given order) join.  Within a group
+ * the reductions meet at the system's own barrier (bounded waits; a wait that
+ * gives up ends that system with PFK_ERR_TIMEOUT) and every CTA combines the
+ * partial sums in rank order, so a system's result depends only on its data
+ * and its CTA count, not on the rest of the batch (bit for bit).  Fill,
+ * iterations, breakdown restarts and the true-residual check run as in
+ * pfk_solve.
+ *  - ops[j]: matrix-free stencil operators; pc: NONE, JACOBI or INNER_PCG in
+ *    FP64 (1..64 inner iterations), the same description for all systems.
+ *  - params: method PFK_PIPEFCG; graph_iters, profile and persistent are
+ *    ignored; barrier_timeout_us as for pfk_solve; history (if set) holds
+ *    nsys consecutive blocks of history_capacity entries.
+ *  - b[j], x[j]: host (ptrs_on_device = 0) or device (1) vectors of length
+ *    n_j; x[j] holds x0 on entry and the solution on exit.
+ *  - ctas_per_system: 1..64, or 0 for about one CTA per 4,096 cells (at most
+ *    64, at most one per x-row).  infos[j].pass_launches reports the CTA
+ *    count used, time_ms the device time of all launches, kernel_launches
+ *    their number.
+ * Returns PFK_OK if every system converged, else the first non-OK status of
+ * a system; PFK_ERR_INVALID for an ineligible system or a system needing more
+ * CTAs than the GPU holds at once. */
+pfk_status pfk_solve_grouped(pfk_context* ctx, int nsys, const pfk_operator* const* ops, const pfk_pc_desc* pc,
+                             const pfk_solve_params* params, const double* const* b, double* const* x,
+                             int ptrs_on_device, int ctas_per_system, pfk_solve_info* infos);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of independent solves                        */
 /* ------------------------------------------------------------------------ */
 
 /* A server accepts solve requests at any time, queues them in arrival order
  * and admits the next one (by pfk_server_params.order: the head of the queue,
- * or the smallest queued request) as soon as a worker is free and the device
+ * or the smallest queued request) as soon as it has room and the device
  * memory the active solves hold (operator, preconditioner scratch, Krylov
  * workspace) plus the new request's estimate fits the budget; a request larger
- * than the budget still runs when nothing else is active.  Each worker owns a
- * CUDA stream and runs whole solves (graph-replayed iterations, Krylov basis
- * resident on the device), so the kernels of active solves overlap on the GPU
- * and requests join while others are running.  A request's arithmetic does not
- * depend on the other requests: its result is bit for bit the one a solve of
- * the same request alone gives.  The server is internally synchronised (any
- * thread may submit and poll). */
+ * than the budget still runs when nothing else is active.  Small requests that
+ * the grouped kernel can run (group_max_n) are advanced together by one
+ * scheduler thread: each gets its own group of CTAs in cooperative launches of
+ * a few iterations, between which finished requests leave and queued ones
+ * join (room = free CTAs of the launch).  The others go to worker threads that
+ * each own a CUDA stream and run whole solves (graph-replayed iterations,
+ * Krylov basis resident on the device); the kernels of both kinds overlap on
+ * the GPU.  A request's arithmetic does not depend on the other requests: its
+ * result is bit for bit the one a solve of the same request alone gives
+ * (pfk_solve_grouped with the same CTA count, or pfk_solve).  The server is
+ * internally synchronised (any thread may submit and poll). */
 typedef struct pfk_server pfk_server;
 
 /* Admission order of queued requests (a scheduling choice; the paper has no
@@ -396,10 +429,16 @@ typedef struct pfk_server pfk_server;
 typedef enum { PFK_SERVE_FIFO = 0, PFK_SERVE_SMALLEST_FIRST = 1 } pfk_serve_order;
 
 typedef struct {
-  int32_t workers;         /* concurrent solves; 0 = 4 */
+  int32_t workers;         /* concurrent whole-GPU solves; 0 = 4 */
   int32_t queue_capacity;  /* queued + active requests; 0 = 4096 */
   int64_t memory_budget;   /* device bytes for active solves; 0 = 80 % of free memory */
   int32_t order;           /* pfk_serve_order; 0 = FIFO */
+  int32_t group_max_n;     /* requests of at most this many unknowns that the grouped
+                              kernel can run (pfk_solve_grouped: stencil, PIPEFCG,
+                              NONE / JACOBI / FP64 INNER_PCG) are advanced together on
+                              it; 0 = 262,144 (64^3), < 0 = never */
+  int32_t group_ctas;      /* CTAs per grouped request, as pfk_solve_grouped's
+                              ctas_per_system; 0 = automatic */
   int32_t reserved;        /* 0 */
 } pfk_server_params;
 

@@ -60,7 +60,8 @@ class InnerSolve(C.Structure):
 
 class ServerParams(C.Structure):
     _fields_ = [("workers", C.c_int32), ("queue_capacity", C.c_int32), ("memory_budget", C.c_int64),
-                ("order", C.c_int32), ("reserved", C.c_int32)]
+                ("order", C.c_int32), ("group_max_n", C.c_int32), ("group_ctas", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 SERVE_ORDERS = {"fifo": 0, "smallest_first": 1}
@@ -112,6 +113,9 @@ _SIGS = {
     "pfk_pc_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "pfk_pc_apply_inner_pcg_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "pfk_solve_batched": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(PcDesc),
+                                    C.POINTER(SolveParams), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                    C.c_int, C.POINTER(SolveInfo)]),
+    "pfk_solve_grouped": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(PcDesc),
                                     C.POINTER(SolveParams), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                                     C.c_int, C.POINTER(SolveInfo)]),
     "pfk_server_create": (C.c_int, [C.c_void_p, C.POINTER(ServerParams), C.POINTER(C.c_void_p)]),
@@ -456,17 +460,54 @@ def solve_batched(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_it
     return xs, out, hs
 
 
+def solve_grouped(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_iters=4, history: int = 0,
+                  ctas_per_system: int = 0, **kw):
+    """Solves independent stencil systems ops[j] x_j = bs[j] with PIPEFCG on the
+    grouped persistent kernel (a group of CTAs per system, the systems sharing
+    cooperative launches).  bs / x0s are NumPy arrays (host path); the
+    preconditioner is FP64.  Returns (xs, infos, histories)."""
+    lib = load()
+    nsys = len(ops)
+    prm = make_params(**kw)
+    hist = None
+    if history:
+        hist = np.full((nsys, history, HISTORY_FIELDS), np.nan)
+        prm.history = hist.ctypes.data
+        prm.history_capacity = history
+    d = PcDesc()
+    d.kind = PC_KINDS[pc_kind]
+    d.inner_iters = int(inner_iters)
+    d.precision = PRECISIONS["fp64"]
+    bh = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+    xs = [np.zeros_like(b) if x0s is None else np.array(x0s[j], dtype=np.float64, copy=True)
+          for j, b in enumerate(bh)]
+    oparr = (C.c_void_p * nsys)(*[op.h.value for op in ops])
+    barr = (C.c_void_p * nsys)(*[b.ctypes.data for b in bh])
+    xarr = (C.c_void_p * nsys)(*[x.ctypes.data for x in xs])
+    infos = (SolveInfo * nsys)()
+    st = lib.pfk_solve_grouped(ctx.h, nsys, oparr, C.byref(d), C.byref(prm), barr, xarr, 0, int(ctas_per_system),
+                               infos)
+    if st not in (PFK_OK, -4, -5, -6):
+        _check(st, ctx.h)
+    out = [infos[j].as_dict() for j in range(nsys)]
+    hs = None
+    if hist is not None:
+        hs = [hist[j][:min(out[j]["history_len"], history)] for j in range(nsys)]
+    return xs, out, hs
+
+
 class Server:
     """Continuous-batching solve server (pfk_server_*): submit requests at any
     time, poll for results.  Requests carry host arrays, which are copied at
     submission; each result is bitwise that of the same request solved alone."""
 
     def __init__(self, ctx: Context, workers: int = 4, queue_capacity: int = 0, memory_budget: int = 0,
-                 order: str = "fifo"):
+                 order: str = "fifo", group_max_n: int = 0, group_ctas: int = 0):
         self.ctx = ctx
         p = ServerParams()
         p.workers, p.queue_capacity, p.memory_budget = int(workers), int(queue_capacity), int(memory_budget)
         p.order = SERVE_ORDERS[order]
+        p.group_max_n, p.group_ctas = int(group_max_n), int(group_ctas)
         h = C.c_void_p()
         _check(load().pfk_server_create(ctx.h, C.byref(p), C.byref(h)), ctx.h)
         self.h = h

@@ -1,0 +1,187 @@
+"""Grouped persistent PIPEFCG (pfk_solve_grouped, and the server's grouped
+path): each system against the oracle (envelope protocol of tests/_parity.py),
+bitwise independence of the batch composition and of the serving order, CTA
+counts from 1 to several per system, the headline regime at 32^3 against the
+stored oracle envelope, and the bounded group barrier's time-out."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov as K
+from oracle import operators as O
+from oracle import preconditioners as PC
+from tests._parity import check_solve, oracle_with_envelope
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    from paper_1511_07226_gb300 import pfk
+    return pfk.Context(0)
+
+
+def _cube(dims, item, log_contrast=2.0):
+    return W.poisson3d_gaussian(dims=dims, ell=3.0, log_contrast=log_contrast, config_id=5, item_id=item)
+
+
+@pytest.mark.parametrize("ctas", [0, 1, 3, 8])
+def test_grouped_systems_match_oracle(ctx, ctas):
+    """Several 3D systems in one grouped batch, 4 inner FP64 Jacobi-PCG
+    iterations, nu_max = 30, rtol 1e-8: every system against the oracle."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 10 + j) for j, d in enumerate([(20, 18, 16), (24, 24, 24), (16, 14, 12)])]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, [c["b"] for c in cs], pc_kind="inner_pcg", inner_iters=4,
+                                         history=3000, ctas_per_system=ctas, mmax=30, rtol=1e-8, maxit=2000,
+                                         max_restarts=50)
+    for c, info, h, x in zip(cs, infos, hists, xs):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.InnerPCG(aop, 4), c["b"],
+                                         K.Params(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50))
+        s = check_solve(h, info, ref, alts, rtol=1e-8, check_restarts=True)
+        assert s["prefix"] >= 5, s
+        if info["status"] == 0:
+            assert np.linalg.norm(c["b"] - aop.apply(x)) <= 1e-8 * np.linalg.norm(c["b"]) * (1 + 1e-6)
+        assert info["pass_launches"] == (ctas or -(-c["b"].size // 4096))
+
+
+def test_grouped_jacobi_2d_and_3d(ctx):
+    """Jacobi preconditioner; 2D and 3D systems in the same batch."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [W.batched2d_system(3, 80, config_id=4), _cube((18, 16, 14), 30), W.batched2d_system(4, 45, config_id=4)]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, [c["b"] for c in cs], pc_kind="jacobi", history=3000,
+                                         ctas_per_system=4, mmax=30, rtol=1e-9, maxit=2500)
+    for c, info, h in zip(cs, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.JacobiPC(aop), c["b"],
+                                         K.Params(mmax=30, rtol=1e-9, maxit=2500))
+        check_solve(h, info, ref, alts, rtol=1e-9)
+
+
+def test_grouped_first_iterations_strict(ctx):
+    """The fill and the first 12 iterations with 6 CTAs per system against the
+    oracle to 1e-10 (before rounding differences grow)."""
+    from paper_1511_07226_gb300 import pfk
+    c = _cube((22, 20, 18), 40)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    xs, infos, hists = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, history=64,
+                                         ctas_per_system=6, mmax=30, rtol=1e-8, maxit=12)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    ref = K.solve("pipefcg", aop, PC.InnerPCG(aop, 4), c["b"], prm=K.Params(mmax=30, rtol=1e-8, maxit=12))
+    rho = ref.rho()
+    assert len(hists[0]) == len(rho) == 13
+    assert np.allclose(hists[0][:, 0], rho, rtol=1e-10, atol=0.0)
+    assert infos[0]["iterations"] == 12 and infos[0]["status_name"] == "not_converged"
+
+
+def test_grouped_composition_and_cta_count(ctx):
+    """A system's result does not depend on the rest of the batch (bitwise);
+    another CTA count changes only the reductions' rounding."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 50 + j) for j, d in enumerate([(16, 16, 16), (30, 20, 10), (12, 12, 40), (20, 20, 20)])]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    kw = dict(pc_kind="inner_pcg", inner_iters=4, history=3000, mmax=30, rtol=1e-8, maxit=2000)
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, [c["b"] for c in cs], ctas_per_system=5, **kw)
+    for j in (1, 3):
+        x1, i1, h1 = pfk.solve_grouped(ctx, [ops[j]], [cs[j]["b"]], ctas_per_system=5, **kw)
+        assert np.array_equal(x1[0], xs[j])
+        assert np.array_equal(h1[0], hists[j], equal_nan=True)
+        assert i1[0]["iterations"] == infos[j]["iterations"]
+    x2, i2, h2 = pfk.solve_grouped(ctx, [ops[0]], [cs[0]["b"]], ctas_per_system=2, **kw)
+    k = 8
+    assert np.allclose(h2[0][:k, 0], hists[0][:k, 0], rtol=1e-11, atol=0.0)
+
+
+def test_grouped_nonzero_initial_guess_and_restart_truncation(ctx):
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 60 + j) for j, d in enumerate([(18, 18, 18), (26, 14, 12)])]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    x0s = [1e-4 * W.random_vector(c["b"].size, 70 + j) for j, c in enumerate(cs)]
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, [c["b"] for c in cs], x0s=x0s, pc_kind="inner_pcg",
+                                         inner_iters=4, history=3000, ctas_per_system=3, mmax=20,
+                                         truncation="restart", rtol=1e-8, maxit=2000, max_restarts=50)
+    for c, x0, info, h in zip(cs, x0s, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.InnerPCG(aop, 4), c["b"],
+                                         K.Params(mmax=20, rtol=1e-8, maxit=2000, max_restarts=50,
+                                                  truncation="restart"), x0=x0)
+        check_solve(h, info, ref, alts, rtol=1e-8)
+
+
+def test_grouped_headline_regime_32cube(ctx):
+    """The 32^3 headline case (contrast 1e6, 4 inner FP64 Jacobi-PCG, nu_max =
+    30, rtol 1e-8, residual-replacement restarts) on the grouped kernel with the
+    automatic CTA count, against the stored oracle envelope."""
+    from paper_1511_07226_gb300 import pfk
+    from tests import _oracle_pool as P
+    from tests._headline_cases import CASES
+    if P.load_stored("pipefcg_32") is None:
+        pytest.skip("no stored envelope for these inputs")
+    cs = CASES["pipefcg_32"]
+    c = P.problem(cs["problem"])
+    prm = cs["prm"]
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    xs, infos, hists = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4,
+                                         history=prm["maxit"] + 400, mmax=30, rtol=1e-8, maxit=prm["maxit"],
+                                         max_restarts=prm["max_restarts"])
+    ref, alts = P.envelope_runs(cs["problem"], cs["method"], cs["pc"], prm, orders=cs["orders"], big=cs["big"],
+                              stored="pipefcg_32")()
+    s = check_solve(hists[0], infos[0], ref, alts, rtol=1e-8, check_restarts=True)
+    assert s["prefix"] >= 10, s
+    assert infos[0]["status_name"] == "ok"
+
+
+def test_grouped_barrier_timeout_is_reported(ctx):
+    """A group barrier that may not wait (barrier_timeout_us < 0) gives up at
+    once: the system ends with PFK_ERR_TIMEOUT, the context stays usable."""
+    from paper_1511_07226_gb300 import pfk
+    c = _cube((16, 16, 16), 80)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    xs, infos, _ = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="jacobi", ctas_per_system=4, mmax=10,
+                                     rtol=1e-8, barrier_timeout_us=-1)
+    assert infos[0]["status"] == -6
+    xs, infos, _ = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="jacobi", ctas_per_system=4, mmax=10,
+                                     rtol=1e-8)
+    assert infos[0]["status"] == 0
+
+
+def test_server_grouped_requests_bitwise_and_oracle(ctx):
+    """Requests served together through the grouped path equal, bit for bit,
+    the same requests solved alone by pfk_solve_grouped; a PIPEGCR request in
+    the same stream goes to a whole-GPU worker and equals pfk_solve alone; one
+    served grouped request is also checked against the oracle's envelope."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 90 + j) for j, d in enumerate([(24, 24, 24), (16, 16, 16), (20, 18, 22), (12, 30, 14)])]
+    kw = dict(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50)
+    srv = pfk.Server(ctx, workers=2)
+    try:
+        tickets = [srv.submit(c["dims"], c["eta"], c["b"], **kw) for c in cs]
+        tg = srv.submit(cs[1]["dims"], cs[1]["eta"], cs[1]["b"], method="pipegcr", **kw)
+        served = [srv.poll(t) for t in tickets]
+        xg, ig, _ = srv.poll(tg)
+    finally:
+        srv.close()
+    for c, (x, info, lat) in zip(cs, served):
+        op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+        x1, i1, _ = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, **kw)
+        assert np.array_equal(x, x1[0])
+        assert info["iterations"] == i1[0]["iterations"] and info["restarts"] == i1[0]["restarts"]
+        assert info["pass_launches"] == i1[0]["pass_launches"] >= 1
+    op = pfk.Operator.stencil(ctx, cs[1]["dims"], cs[1]["eta"])
+    pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
+    x1, i1, _ = pfk.solve(ctx, op, pc, cs[1]["b"], method="pipegcr", **kw)
+    assert np.array_equal(xg, x1) and ig["iterations"] == i1["iterations"]
+    # the served solution of the first request against the oracle's
+    c = cs[0]
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.InnerPCG(aop, 4), c["b"],
+                                     K.Params(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50))
+    x, info, _ = served[0]
+    if ref.status == "converged" and all(a.status == "converged" for a in alts):
+        assert info["status_name"] == "ok"
+        band = 2 * max(abs(a.iterations - ref.iterations) for a in alts) + 0.05 * ref.iterations + 2
+        assert abs(info["iterations"] - ref.iterations) <= band
+        err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-5, err
