@@ -273,9 +273,9 @@ def main():
                     help="only the FP64 FMA-rate probe (pfk_probe_fp64_fma), three times, as JSON")
     ap.add_argument("--block-threads", type=int, default=256,
                     help="threads per block of the --case batched profiler case")
-    ap.add_argument("--extras", default="config1,fcg,pipegcr,nu_sweep,stokes,batched,fgmres256,serve,serve_sweep",
+    ap.add_argument("--extras", default="config1,fcg,pipegcr,nu_sweep,stokes,batched,grouped,fgmres256,serve,serve_sweep",
                     help="comma-separated secondary measurements (config1, fcg, pipegcr, nu_sweep, stokes, batched, "
-                         "fgmres256, serve, serve_sweep) or 'none'")
+                         "grouped, fgmres256, serve, serve_sweep) or 'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
@@ -777,14 +777,19 @@ def extra_fgmres256(ctx, dev, args) -> dict:
     return out
 
 
-def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo") -> dict:
-    """Replays requests through a fresh server (admission `order`) at their
-    arrival times scaled by rate_scale (2 = twice as far apart); returns latency
-    and throughput."""
+GROUP_MAX_N = 262144   # the server's default: requests up to 64^3 unknowns run grouped when eligible
+
+
+def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo", group_max_n=0) -> dict:
+    """Replays requests through a fresh server (admission `order`; grouped
+    kernel for eligible requests up to group_max_n unknowns, 0 = the server's
+    default, < 0 = off) at their arrival times scaled by rate_scale (2 = twice
+    as far apart); returns latency and throughput, overall and for the grouped
+    requests."""
     import workloads as W
     from paper_1511_07226_gb300 import pfk
     meth = {0: "pipefcg", 1: "pipegcr", 2: "pipefgmres"}
-    srv = pfk.Server(ctx, workers=workers, order=order)
+    srv = pfk.Server(ctx, workers=workers, order=order, group_max_n=group_max_n)
     kw = dict(mmax=30, rtol=1e-8, maxit=20000, max_restarts=MAX_RESTARTS)
     # warm-up: one small request per method (graphs, module loading)
     for m in meth.values():
@@ -804,7 +809,14 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo") -> di
     its = [int(res[1]["iterations"]) for res in results]
     unk_its = float(sum(int(np.prod(p["dims"])) * i for p, i in zip(probs, its)))
     unknowns = int(sum(r["side"] ** 3 for r in reqs))
-    return {"workers": workers, "order": order, "requests": len(reqs),
+    gmax = GROUP_MAX_N if group_max_n == 0 else max(group_max_n, 0)
+    grouped = [j for j, r in enumerate(reqs) if meth[r["method"]] == "pipefcg" and r["side"] ** 3 <= gmax]
+    small = [j for j, r in enumerate(reqs) if r["side"] ** 3 <= GROUP_MAX_N]
+    return {"workers": workers, "order": order, "group_max_n": gmax, "requests": len(reqs),
+            "grouped_requests": len(grouped),
+            "grouped_p50_latency_ms": float(np.percentile(lat[grouped], 50)) if grouped else None,
+            "small_requests": len(small),
+            "small_p50_latency_ms": float(np.percentile(lat[small], 50)) if small else None,
             "converged": int(sum(res[1]["status_name"] == "ok" for res in results)),
             "offered_rate_per_s": len(reqs) / max(rate_scale * (reqs[-1]["t"] - reqs[0]["t"]), 1e-9),
             "solves_per_s": len(reqs) / wall, "unknowns_per_s": unknowns / wall,
@@ -825,34 +837,77 @@ def extra_serve(ctx, dev, args) -> dict:
     probs = [W.request_problem(r) for r in reqs]
     out = _serve_replay(ctx, reqs, probs, args.serve_workers)
     out["workload"] = f"first {len(reqs)} requests of the seeded stream, replayed at their arrival times"
-    # the same replay with the smallest queued request admitted first
+    # the same replay with every request on the whole-GPU workers, and with
+    # the smallest queued request admitted first
+    out["whole_gpu_only"] = _serve_replay(ctx, reqs, probs, args.serve_workers, group_max_n=-1)
     out["smallest_first"] = _serve_replay(ctx, reqs, probs, args.serve_workers, order="smallest_first")
     out["oracle_per_request"] = oracle_request_sample(reqs, probs, out.pop("_iterations"))
+    out["whole_gpu_only"].pop("_iterations", None)
     out["smallest_first"].pop("_iterations", None)
-    out["one_cta_vs_whole_gpu"] = one_cta_vs_whole_gpu(ctx)
     return out
 
 
-def one_cta_vs_whole_gpu(ctx) -> dict:
-    """Why served requests run the whole-GPU path: the time per PIPEFCG
-    iteration of one small 3D request (4 inner FP64 PCG iterations) in the
-    persistent batched kernel (one CTA owns the system) against the whole-GPU
-    graph path, at 100 iterations each."""
+def grouped_fp64_per_unknown_iteration(nu: int, inner: int = 4) -> float:
+    """FP64 instructions (DFMA / DMUL / DADD, one each) per unknown of one
+    PIPEFCG iteration on the grouped kernel, from its source: the pass 5 nu + 9
+    (four MAXPY FMAs and one window-dot FMA per window slot; the x, r, u, w
+    advance, t = w - r and four dot FMAs), the 7-point operator with its
+    advection terms 13, and `inner` Jacobi-PCG iterations 17 + 20 (inner - 1)
+    + 2 (first residual, dot and search direction with s = A p; per further
+    iteration the r, x and p updates, two dots and s = A p; the last x update
+    and m = u + x)."""
+    return 5.0 * nu + 9.0 + 13.0 + 17.0 + 20.0 * (inner - 1) + 2.0
+
+
+def extra_grouped(ctx, dev, args) -> dict:
+    """Small 3D requests on the grouped kernel against the whole-GPU graph
+    path: per side, enough systems to fill one cooperative launch (about 4,096
+    cells per CTA, three CTAs per SM) run 100 PIPEFCG iterations each (nu_max =
+    30, 4 inner FP64 Jacobi-PCG iterations, contrast 1e2) in one
+    pfk_solve_grouped call; the whole-GPU path solves two of them one after the
+    other.  Throughput in system-iterations per second, and the grouped
+    kernel's FP64 instruction rate (the count of grouped_fp64_per_unknown_iteration
+    over the launches' device time) against the measured FP64 FMA rate."""
     import workloads as W
     from paper_1511_07226_gb300 import pfk
+    fp64_peak = pfk.probe_fp64_fma(ctx)["tflops"] * 1e12 / 2.0   # FMA instructions per second, measured live
+    kw = dict(mmax=30, rtol=1e-300, maxit=100, max_restarts=0)
+    nus = [min(i, 30) for i in range(1, 101)]
     rows = []
-    for side in (24, 32, 48):
-        p = W.poisson3d_gaussian(n=side, ell=4.0, log_contrast=2.0, config_id=5, item_id=800 + side)
-        op = pfk.Operator.stencil(ctx, p["dims"], p["eta"])
-        kw = dict(mmax=30, rtol=1e-300, maxit=100, max_restarts=0)
-        pfk.solve_batched(ctx, [op], [p["b"]], pc_kind="inner_pcg", inner_iters=4, precision="fp64", **kw)
-        _, bi, _ = pfk.solve_batched(ctx, [op], [p["b"]], pc_kind="inner_pcg", inner_iters=4, precision="fp64", **kw)
-        pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
-        pfk.solve(ctx, op, pc, p["b"], **kw)
-        _, gi, _ = pfk.solve(ctx, op, pc, p["b"], **kw)
-        rows.append({"side": side, "one_cta_ms_per_iteration": bi[0]["time_ms"] / max(bi[0]["iterations"], 1),
-                     "whole_gpu_ms_per_iteration": gi["time_ms"] / max(gi["iterations"], 1)})
-    return {"note": "PIPEFCG nu_max=30, 4 inner FP64 Jacobi-PCG, 100 iterations each", "runs": rows}
+    for side in (24, 32, 48, 64):
+        n = side ** 3
+        nblk = min(64, -(-n // 4096))
+        count = max(1, min(96, (3 * 152) // nblk))
+        ps = [W.poisson3d_gaussian(n=side, ell=4.0, log_contrast=2.0, config_id=5, item_id=700 + j)
+              for j in range(count)]
+        ops = [pfk.Operator.stencil(ctx, p["dims"], p["eta"]) for p in ps]
+        bs = [p["b"] for p in ps]
+        pfk.solve_grouped(ctx, ops[:1], bs[:1], pc_kind="inner_pcg", inner_iters=4, **kw)
+        t0 = time.perf_counter()
+        _, gi, _ = pfk.solve_grouped(ctx, ops, bs, pc_kind="inner_pcg", inner_iters=4, **kw)
+        wall = time.perf_counter() - t0
+        g_ms = gi[0]["time_ms"]
+        its = sum(i["iterations"] for i in gi)
+        instr = sum(grouped_fp64_per_unknown_iteration(nu) for nu in nus) * n * count
+        whole = []
+        for op, b in zip(ops[:2], bs[:2]):
+            pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
+            pfk.solve(ctx, op, pc, b, **kw)
+            _, wi, _ = pfk.solve(ctx, op, pc, b, **kw)
+            whole.append(wi["time_ms"] / max(wi["iterations"], 1))
+        w_ms = float(np.mean(whole))
+        rows.append({"side": side, "systems": count, "ctas_per_system": gi[0]["pass_launches"],
+                     "launches": gi[0]["kernel_launches"], "grouped_kernel_ms": g_ms, "grouped_wall_ms": wall * 1e3,
+                     "grouped_ms_per_iteration_per_system": g_ms / 101.0,
+                     "grouped_system_iterations_per_s": its / (g_ms / 1e3),
+                     "whole_gpu_ms_per_iteration": w_ms, "whole_gpu_system_iterations_per_s": 1e3 / w_ms,
+                     "throughput_ratio": (its / (g_ms / 1e3)) / (1e3 / w_ms),
+                     "fp64_instr_per_s": instr / (g_ms / 1e3),
+                     "fp64_frac_of_measured": instr / (g_ms / 1e3) / fp64_peak})
+    return {"workload": "3D requests at contrast 1e2, PIPEFCG nu_max=30, 4 inner FP64 Jacobi-PCG, 100 iterations "
+                        "per system (plus the fill); grouped: as many systems as one launch holds",
+            "fp64_peak_instr_per_s": fp64_peak,
+            "fp64_peak_note": "FP64 FMA-chain probe (pfk_probe_fp64_fma) run in this leg, FLOP/s / 2", "runs": rows}
 
 
 def oracle_request_sample(reqs, probs, iterations, count: int = 3) -> dict:
@@ -916,7 +971,7 @@ STOKES_N = 256
 STOKES_INNER_RTOL = 1e-3
 STOKES_INNER_MAXIT = 500
 
-EXTRAS = {"config1": extra_config1, "fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "stokes": extra_stokes,
+EXTRAS = {"grouped": extra_grouped, "config1": extra_config1, "fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "stokes": extra_stokes,
           "serve_sweep": extra_serve_sweep, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
 
 
