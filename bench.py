@@ -265,10 +265,13 @@ def main():
     ap.add_argument("--maxit", type=int, default=10000)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--method", default="pipefcg", help="method of the --ncu-case solve")
-    ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase", "batched", "config1"],
+    ap.add_argument("--case", default="gaussian", choices=["gaussian", "two_phase", "batched", "config1", "grouped"],
                     help="--ncu-case problem: Gaussian-field Poisson (4 inner PCG), two-phase advection "
-                         "(8 Chebyshev sweeps), the first --n systems of the batched workload, or the 64x64 CSR "
-                         "problem with Jacobi (--method pipefcg or fcg, persistent path; --maxit iterations)")
+                         "(8 Chebyshev sweeps), the first --n systems of the batched workload, the 64x64 CSR "
+                         "problem with Jacobi (--method pipefcg or fcg, persistent path; --maxit iterations), or "
+                         "--systems n^3 systems on the grouped kernel (--method pipefcg or pipegcr, --maxit "
+                         "iterations each)")
+    ap.add_argument("--systems", type=int, default=57, help="systems of the --case grouped profiler case")
     ap.add_argument("--fp64-probe", action="store_true",
                     help="only the FP64 FMA-rate probe (pfk_probe_fp64_fma), three times, as JSON")
     ap.add_argument("--block-threads", type=int, default=256,
@@ -297,6 +300,20 @@ def main():
                                persistent="on")
         print(json.dumps({"ncu_case": "config1", "method": args.method, "iterations": info["iterations"],
                           "status": info["status_name"]}))
+        return
+    if args.ncu_case and args.case == "grouped":
+        import workloads as W
+        from paper_1511_07226_gb300 import pfk
+        ctx = pfk.Context(0)
+        ps = [W.poisson3d_gaussian(n=args.n, ell=4.0, log_contrast=2.0, config_id=5, item_id=700 + j)
+              for j in range(args.systems)]
+        ops = [pfk.Operator.stencil(ctx, p["dims"], p["eta"]) for p in ps]
+        _, infos, _ = pfk.solve_grouped(ctx, ops, [p["b"] for p in ps], pc_kind="inner_pcg", inner_iters=4,
+                                        method=args.method, mmax=30, rtol=1e-300, maxit=args.maxit,
+                                        max_restarts=0)
+        print(json.dumps({"ncu_case": "grouped", "systems": len(ops), "ctas_per_system": infos[0]["pass_launches"],
+                          "launches": infos[0]["kernel_launches"],
+                          "iterations": int(sum(i["iterations"] for i in infos))}))
         return
     if args.ncu_case and args.case == "batched":
         import workloads as W
@@ -810,7 +827,7 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo", group
     unk_its = float(sum(int(np.prod(p["dims"])) * i for p, i in zip(probs, its)))
     unknowns = int(sum(r["side"] ** 3 for r in reqs))
     gmax = GROUP_MAX_N if group_max_n == 0 else max(group_max_n, 0)
-    grouped = [j for j, r in enumerate(reqs) if meth[r["method"]] == "pipefcg" and r["side"] ** 3 <= gmax]
+    grouped = [j for j, r in enumerate(reqs) if meth[r["method"]] in ("pipefcg", "pipegcr") and r["side"] ** 3 <= gmax]
     small = [j for j, r in enumerate(reqs) if r["side"] ** 3 <= GROUP_MAX_N]
     return {"workers": workers, "order": order, "group_max_n": gmax, "requests": len(reqs),
             "grouped_requests": len(grouped),

@@ -1,5 +1,5 @@
-// Grouped persistent PIPEFCG: several stencil systems advanced together by one
-// cooperative launch, each system by its own group of CTAs.
+// Grouped persistent PIPEFCG / PIPEGCR: several stencil systems advanced
+// together by one cooperative launch, each system by its own group of CTAs.
 //
 // A system of n cells belongs to a group of C CTAs (by default about 4,096
 // cells per CTA, at most kGrpMaxCtas); the CTA of rank q owns a contiguous
@@ -9,7 +9,9 @@
 // previous iteration, the advance of x, r, u, w, the dots gamma_i, delta_i,
 // ||r_i||^2 and the window dots <u_i, s_k>), the preconditioner (none,
 // Jacobi, or k inner Jacobi-PCG iterations, Alg. 3, in FP64) and the
-// operator.  A reduction writes one partial row per CTA; the CTAs meet at the
+// operator.  PIPEGCR (Alg. 11) splits the pass in two: the deferred MAXPYs
+// with the advance of x, r, u, then w_i = A u_i with the dots gamma_i =
+// <r_i, w_i>, delta_i = <w_i, w_i>, ||r_i||^2 and <w_i, s_k>.  A reduction writes one partial row per CTA; the CTAs meet at the
 // system's own barrier (an arrival counter and a generation word of that
 // system, with bounded waits) and every CTA sums the rows in rank order, so
 // all CTAs of the group hold bitwise the same scalars and run the scalar
@@ -48,6 +50,7 @@ constexpr int kGrpMaxInner = 64;             // inner PCG iterations
 enum GrpPhase { kGStart = 0, kGFill = 1, kGIter = 2, kGDone = 3 };
 
 struct GrpParams {
+  int method;                 // PFK_PIPEFCG or PFK_PIPEGCR
   int mmax, truncation, norm, maxit, max_restarts, true_check;
   double rtol, atol;
   int pc_kind, pc_inner;
@@ -381,6 +384,79 @@ __device__ __forceinline__ void grp_push_history(const GrpSys& S, GrpCta* g, dou
   st->hist_len += 1;
 }
 
+// Scalar phase of iteration i (thread 0 of every CTA): convergence test on
+// rho_i first (the listings' order), then beta_{i,k} = -c_k / eta_k for the
+// window k = i - nu_i .. i - 1 (cw(jj) gives c for k = i - nu_i + jj), eta_i =
+// delta_i - sum_k beta_{i,k}^2 eta_k (k ascending), alpha_i = gamma_i / eta_i;
+// eta_i <= 0 is a norm breakdown.
+template <typename CW>
+__device__ void grp_scalar_phase(const GrpSys& S, GrpCta* g, int i, double gamma, double delta, double rr,
+                                 const CW& cw) {
+  const GrpParams& P = S.P;
+  GrpState* st = &g->st;
+  const int slots = P.mmax + 1;
+  st->it += 1;
+  st->i = i;
+  st->gamma = gamma;
+  st->delta = delta;
+  const double rho = grp_rho(P, gamma, rr);
+  st->rho = rho;
+  const int hslot = st->hist_len;
+  grp_push_history(S, g, rho, sqrt(rr), nan(""), nan(""));
+  if (!isfinite(rho)) {
+    st->status = kNonFinite;
+    return;
+  }
+  if (rho <= st->target) {
+    st->status = kConverged;
+    return;
+  }
+  const int nu = nu_window(i, P.mmax, P.truncation);
+  double sumb = 0.0;
+  for (int jj = 0; jj < nu; ++jj) {
+    const double ek = st->eta_ring[(i - nu + jj) % slots];
+    const double bb = -cw(jj) / ek;
+    st->beta[jj] = bb;
+    sumb += bb * bb * ek;
+  }
+  const double eta = delta - sumb;
+  const double al = eta != 0.0 ? gamma / eta : nan("");
+  st->eta = eta;
+  st->alpha = al;
+  st->nw = nu;
+  st->eta_ring[i % slots] = eta;
+  if (g->rank == 0 && S.hist && hslot < S.hist_cap) {
+    S.hist[(size_t)hslot * PFK_HISTORY_FIELDS + 2] = eta;
+    S.hist[(size_t)hslot * PFK_HISTORY_FIELDS + 3] = al;
+  }
+  if (eta <= 0.0) st->status = kBreakdown;
+  else if (st->it >= P.maxit) st->status = kMaxit;
+}
+
+// Combines a CTA's partial row (nd values in s_row, shared) over the group
+// into g->s_tot: directly with one CTA, else through the partial rows and the
+// system's barrier, summed in rank order.
+__device__ void grp_combine_row(const GrpSys& S, GrpCta* g, int nd, const double* s_warp) {
+  const int par = g->par;
+  if (threadIdx.x < nd) {
+    double v = 0.0;
+    for (int w = 0; w < kGrpThreads / 32; ++w) v += s_warp[w * nd + threadIdx.x];
+    if (g->nblk == 1) g->s_tot[threadIdx.x] = v;
+    else S.part[((size_t)par * g->nblk + g->rank) * kGrpNd + threadIdx.x] = v;
+  }
+  if (g->nblk > 1) {
+    grp_barrier(S, g);
+    if (threadIdx.x < nd) {
+      const double* pp = S.part + (size_t)par * g->nblk * kGrpNd + threadIdx.x;
+      double v = 0.0;
+      for (int b = 0; b < g->nblk; ++b) v += __ldcg(pp + (size_t)b * kGrpNd);
+      g->s_tot[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) g->par = par ^ 1;
+  }
+  __syncthreads();
+}
+
 // The fused pass of iteration i (the same statements as the single-system
 // pass: the deferred MAXPYs p, s, q, z of iteration i-1 from u, w, m, n and
 // the window; x, r, u, w advanced with alpha_{i-1}; t = w - r; the dots
@@ -480,71 +556,143 @@ __device__ void grp_pass(const GrpSys& S, GrpCta* g, double* smem) {
     if (lane < nwp) s_red[warp * nd + 4 + lane] = gw;
   }
   __syncthreads();
-  const int par = g->par;
-  if (threadIdx.x < nd) {
-    double v = 0.0;
-    for (int w = 0; w < T / 32; ++w) v += s_red[w * nd + threadIdx.x];
-    if (g->nblk == 1) g->s_tot[threadIdx.x] = v;
-    else S.part[((size_t)par * g->nblk + g->rank) * kGrpNd + threadIdx.x] = v;
-  }
-  if (g->nblk > 1) {
-    grp_barrier(S, g);
-    if (threadIdx.x < nd) {
-      const double* pp = S.part + (size_t)par * g->nblk * kGrpNd + threadIdx.x;
-      double v = 0.0;
-      for (int b = 0; b < g->nblk; ++b) v += __ldcg(pp + (size_t)b * kGrpNd);
-      g->s_tot[threadIdx.x] = v;
-    }
-    if (threadIdx.x == 0) g->par = par ^ 1;
-  }
-  __syncthreads();
+  grp_combine_row(S, g, nd, s_red);
   if (threadIdx.x == 0) {
-    const GrpParams& P = S.P;
+    // the window dots of iteration i: <u_i, s_k> for the previous window's
+    // slots (columns 4..) and the new s_{i-1} (column 3)
     const double* tot = g->s_tot;
     const int i = iprev + 1;
-    const double gamma = tot[0], delta = tot[1], rr = tot[2];
-    st->it += 1;
-    st->i = i;
-    st->gamma = gamma;
-    st->delta = delta;
-    const double rho = grp_rho(P, gamma, rr);
-    st->rho = rho;
-    const int hslot = st->hist_len;
-    grp_push_history(S, g, rho, sqrt(rr), nan(""), nan(""));
-    if (!isfinite(rho)) {
-      st->status = kNonFinite;
-    } else if (rho <= st->target) {
-      st->status = kConverged;
-    } else {
-      const int nu = nu_window(i, P.mmax, P.truncation);
-      const int off = nwp + 1 - nu;
-      double sumb = 0.0;
-      for (int jj = 0; jj < nu; ++jj) {
-        const int src = off + jj;
-        const double cc = src < nwp ? tot[4 + src] : tot[3];
-        const double ek = st->eta_ring[(i - nu + jj) % slots];
-        const double bb = -cc / ek;
-        st->beta[jj] = bb;
-        sumb += bb * bb * ek;
-      }
-      const double eta = delta - sumb;
-      const double al = eta != 0.0 ? gamma / eta : nan("");
-      st->eta = eta;
-      st->alpha = al;
-      st->nw = nu;
-      st->eta_ring[i % slots] = eta;
-      if (g->rank == 0 && S.hist && hslot < S.hist_cap) {
-        S.hist[(size_t)hslot * PFK_HISTORY_FIELDS + 2] = eta;
-        S.hist[(size_t)hslot * PFK_HISTORY_FIELDS + 3] = al;
-      }
-      if (eta <= 0.0) st->status = kBreakdown;
-      else if (st->it >= P.maxit) st->status = kMaxit;
-    }
+    const int nu = nu_window(i, S.P.mmax, S.P.truncation);
+    const int off = nwp + 1 - nu;
+    grp_scalar_phase(S, g, i, tot[0], tot[1], tot[2], [&](int jj) {
+      const int src = off + jj;
+      return src < nwp ? tot[4 + src] : tot[3];
+    });
   }
   __syncthreads();
 }
 
-// Pipeline fill (Alg. 8, before the loop) from the current x.
+// PIPEGCR (Alg. 11), first part of iteration i: the deferred MAXPYs of
+// iteration i-1 (p, s, q from u, w, m and the window) into ring slot i-1,
+// then x_i, r_i and u_i with alpha_{i-1}; ends at the system's barrier (the
+// operator reads the neighbours' u_i next).
+__device__ void grp_gcr_advance(const GrpSys& S, GrpCta* g) {
+  GrpState* st = &g->st;
+  const int64_t n = S.n;
+  double* vr = S.ws;
+  double* vu = vr + n;
+  const double* vw = vu + n;
+  const double* vm = vw + n;
+  const int slots = S.P.mmax + 1;
+  double* Pr = S.ws + 7 * n;
+  double* Sr = Pr + (int64_t)slots * n;
+  double* Qr = Sr + (int64_t)slots * n;
+  const int iprev = st->i;
+  const int nwp = st->nw;
+  const double alpha = st->alpha;
+  if (threadIdx.x < nwp) {
+    g->s_off[threadIdx.x] = (size_t)((iprev - nwp + (int)threadIdx.x) % slots) * (size_t)n;
+    g->s_beta[threadIdx.x] = st->beta[threadIdx.x];
+  }
+  __syncthreads();
+  const size_t coff = (size_t)(iprev % slots) * (size_t)n;
+  GRP_ELEMS(S, g, e) {
+    const double u0 = vu[e];
+    double p = u0, sv = vw[e], q = vm[e];
+#pragma unroll 4
+    for (int jj = 0; jj < nwp; ++jj) {
+      const size_t o = g->s_off[jj] + e;
+      const double bb = g->s_beta[jj];
+      p = fma(bb, Pr[o], p);
+      sv = fma(bb, Sr[o], sv);
+      q = fma(bb, Qr[o], q);
+    }
+    Pr[coff + e] = p;
+    Sr[coff + e] = sv;
+    Qr[coff + e] = q;
+    S.x[e] = fma(alpha, p, S.x[e]);
+    vr[e] = fma(-alpha, sv, vr[e]);
+    vu[e] = fma(-alpha, q, u0);
+  }
+  grp_barrier(S, g);
+}
+
+// PIPEGCR, second part: w_i = A u_i on the CTA's rows and t = w_i - r_i; the
+// iteration's one reduction -- gamma_i = <r_i, w_i>, delta_i = <w_i, w_i>,
+// ||r_i||^2 and <w_i, s_k> for the window k = i - nu_i .. i - 1 (transposed
+// through shared memory as in the PIPEFCG pass) -- and the scalar phase.
+__device__ void grp_gcr_dots(const GrpSys& S, GrpCta* g, double* smem) {
+  constexpr int T = kGrpThreads;
+  GrpState* st = &g->st;
+  const int64_t n = S.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* vr = S.ws;
+  const double* vu = vr + n;
+  double* vw = (double*)vu + n;
+  double* vt = S.ws + 5 * n;
+  const int slots = S.P.mmax + 1;
+  const double* Sr = S.ws + 7 * n + (int64_t)slots * n;
+  const int i = st->i + 1;
+  const int nu = nu_window(i, S.P.mmax, S.P.truncation);
+  GRP_ROWS(S, g, c, ii, j, k) {
+    const double wv = grp_row(S, vu, c, ii, j, k);
+    vw[c] = wv;
+    vt[c] = wv - vr[c];
+  }
+  if (threadIdx.x < nu) g->s_off[threadIdx.x] = (size_t)((i - nu + (int)threadIdx.x) % slots) * (size_t)n;
+  __syncthreads();
+  double* s_sk = smem;
+  double* s_w = s_sk + kGrpNW * (T + 1);
+  double* s_red = s_w + T;
+  double* my = s_sk + threadIdx.x;
+  const double* ww = s_w + warp * 32;
+  const double* lrow = s_sk + lane * (T + 1) + warp * 32;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0, gw = 0.0;
+  const int64_t e_lo = g->row_lo * S.nx, e_hi = g->row_hi * S.nx;
+  for (int64_t base = e_lo; base < e_hi; base += T) {
+    const int64_t e = base + threadIdx.x;
+    double wv = 0.0;
+    if (e < e_hi) {
+      wv = vw[e];
+      const double rv = vr[e];
+      g0 = fma(rv, wv, g0);
+      g1 = fma(wv, wv, g1);
+      g2 = fma(rv, rv, g2);
+      for (int jj = 0; jj < nu; ++jj) my[jj * (T + 1)] = Sr[g->s_off[jj] + e];
+    } else {
+      for (int jj = 0; jj < nu; ++jj) my[jj * (T + 1)] = 0.0;
+    }
+    s_w[threadIdx.x] = wv;
+    __syncwarp();
+    if (lane < nu) {
+      double c = gw;
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) c = fma(ww[t], lrow[t], c);
+      gw = c;
+    }
+    __syncwarp();
+  }
+  const int nd = nu + 4;
+  {
+    const double a0 = warp_sum(g0), a1 = warp_sum(g1), a2 = warp_sum(g2);
+    if (lane == 0) {
+      s_red[warp * nd + 0] = a0;
+      s_red[warp * nd + 1] = a1;
+      s_red[warp * nd + 2] = a2;
+      s_red[warp * nd + 3] = 0.0;
+    }
+    if (lane < nu) s_red[warp * nd + 4 + lane] = gw;
+  }
+  __syncthreads();
+  grp_combine_row(S, g, nd, s_red);
+  if (threadIdx.x == 0) {
+    const double* tot = g->s_tot;
+    grp_scalar_phase(S, g, i, tot[0], tot[1], tot[2], [&](int jj) { return tot[4 + jj]; });
+  }
+  __syncthreads();
+}
+
+// Pipeline fill (Alg. 8 / Alg. 11, before the loop) from the current x.
 __device__ void grp_fill(const GrpSys& S, GrpCta* g, double* smem) {
   GrpState* st = &g->st;
   const int64_t n = S.n;
@@ -554,15 +702,19 @@ __device__ void grp_fill(const GrpSys& S, GrpCta* g, double* smem) {
   double* vm = vw + n;
   double* vn = vm + n;
   double* s_red = smem;
+  const bool gcr = S.P.method == PFK_PIPEGCR;
   grp_apply(S, g, S.x, vr, S.b);             // r_0 = b - A x_0
   grp_pc(S, g, vr, vu, nullptr, s_red);      // u_0 = B(r_0) = p_0
-  grp_apply(S, g, vu, vw, nullptr);          // w_0 = A p_0
-  grp_pc(S, g, vw, vm, nullptr, s_red);      // m_0 = B(w_0)
-  grp_apply(S, g, vm, vn, nullptr);          // n_0 = A m_0
+  grp_apply(S, g, vu, vw, nullptr);          // w_0 = A p_0 (Alg. 11: s_0)
+  grp_pc(S, g, vw, vm, nullptr, s_red);      // m_0 = B(w_0) (Alg. 11: q_0)
+  if (!gcr) grp_apply(S, g, vm, vn, nullptr);   // n_0 = A m_0
+  // Alg. 8: gamma_0 = <u_0, r_0>, eta_0 = delta_0 = <u_0, w_0>;
+  // Alg. 11: gamma_0 = <r_0, s_0>, eta_0 = <s_0, s_0>; and ||r_0||^2
   double acc[3] = {0.0, 0.0, 0.0};
   GRP_ELEMS(S, g, e) {
-    acc[0] = fma(vu[e], vr[e], acc[0]);
-    acc[1] = fma(vu[e], vw[e], acc[1]);
+    const double a = gcr ? vw[e] : vu[e];
+    acc[0] = fma(a, vr[e], acc[0]);
+    acc[1] = fma(a, vw[e], acc[1]);
     acc[2] = fma(vr[e], vr[e], acc[2]);
   }
   grp_sum<3>(S, g, acc, s_red);
@@ -697,7 +849,13 @@ __global__ void __launch_bounds__(kGrpThreads, 3)
       if (st->status != kRun) grp_after_cycle(S, &g, smem);
       continue;
     }
-    grp_pass(S, &g, smem);
+    const bool gcr = S.P.method == PFK_PIPEGCR;
+    if (gcr) {
+      grp_gcr_advance(S, &g);
+      grp_gcr_dots(S, &g, smem);
+    } else {
+      grp_pass(S, &g, smem);
+    }
     if (st->status != kRun) {
       grp_after_cycle(S, &g, smem);
       continue;
@@ -707,7 +865,7 @@ __global__ void __launch_bounds__(kGrpThreads, 3)
     double* vn = S.ws + 4 * n;
     double* vt = S.ws + 5 * n;
     grp_pc(S, &g, vt, vm, vu, smem);        // m_i = u_i + B(w_i - r_i)
-    grp_apply(S, &g, vm, vn, nullptr);      // n_i = A m_i
+    if (!gcr) grp_apply(S, &g, vm, vn, nullptr);   // n_i = A m_i (Alg. 8)
   }
   if (st->phase == kGDone && !g.abort && (isnan(st->rtrue) || st->result != PFK_OK)) {
     grp_true_residual(S, &g, smem);
@@ -739,7 +897,8 @@ size_t grp_smem_bytes() {
 
 bool group_method_eligible(const pfk_pc_desc* pcd, const pfk_solve_params* prm, const char** why) {
   const char* w = nullptr;
-  if (!prm || prm->method != PFK_PIPEFCG) w = "the grouped solve runs PFK_PIPEFCG";
+  if (!prm || (prm->method != PFK_PIPEFCG && prm->method != PFK_PIPEGCR))
+    w = "the grouped solve runs PFK_PIPEFCG or PFK_PIPEGCR";
   else if (prm->mmax < 1 || prm->mmax > PFK_MAX_MMAX) w = "mmax out of range";
   else if (pcd && !(pcd->kind == PFK_PC_NONE || pcd->kind == PFK_PC_JACOBI ||
                     (pcd->kind == PFK_PC_INNER_PCG && pcd->precision == PFK_FP64 && pcd->inner_iters >= 1 &&
@@ -893,6 +1052,7 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
   S.hist = hist_dev;
   S.hist_cap = hist_dev ? hist_cap : 0;
   GrpParams& P = S.P;
+  P.method = prm->method;
   P.mmax = prm->mmax; P.truncation = prm->truncation; P.norm = prm->norm; P.maxit = prm->maxit;
   P.max_restarts = prm->max_restarts; P.true_check = prm->true_residual_check;
   P.rtol = prm->rtol; P.atol = prm->atol;

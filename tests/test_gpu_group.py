@@ -1,5 +1,5 @@
-"""Grouped persistent PIPEFCG (pfk_solve_grouped, and the server's grouped
-path): each system against the oracle (envelope protocol of tests/_parity.py),
+"""Grouped persistent PIPEFCG and PIPEGCR (pfk_solve_grouped, and the
+server's grouped path): each system against the oracle (envelope protocol of tests/_parity.py),
 bitwise independence of the batch composition and of the serving order, CTA
 counts from 1 to several per system, the headline regime at 32^3 against the
 stored oracle envelope, and the bounded group barrier's time-out."""
@@ -44,6 +44,40 @@ def test_grouped_systems_match_oracle(ctx, ctas):
         if info["status"] == 0:
             assert np.linalg.norm(c["b"] - aop.apply(x)) <= 1e-8 * np.linalg.norm(c["b"]) * (1 + 1e-6)
         assert info["pass_launches"] == (ctas or -(-c["b"].size // 4096))
+
+
+@pytest.mark.parametrize("ctas", [0, 3])
+def test_grouped_pipegcr_matches_oracle(ctx, ctas):
+    """PIPEGCR (Alg. 11) on the grouped kernel, 4 inner FP64 Jacobi-PCG
+    iterations, against the oracle."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 20 + j) for j, d in enumerate([(20, 18, 16), (16, 16, 24)])]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, [c["b"] for c in cs], pc_kind="inner_pcg", inner_iters=4,
+                                         history=3000, ctas_per_system=ctas, method="pipegcr", mmax=30, rtol=1e-8,
+                                         maxit=2000, max_restarts=50)
+    for c, info, h in zip(cs, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipegcr", aop, lambda: PC.InnerPCG(aop, 4), c["b"],
+                                         K.Params(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50))
+        s = check_solve(h, info, ref, alts, rtol=1e-8, check_restarts=True)
+        assert s["prefix"] >= 5, s
+
+
+def test_grouped_pipegcr_first_iterations_strict(ctx):
+    """PIPEGCR's fill and first 12 iterations with 5 CTAs, Jacobi, against the
+    oracle to 1e-10."""
+    from paper_1511_07226_gb300 import pfk
+    c = _cube((20, 22, 18), 45)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    xs, infos, hists = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="jacobi", history=64, ctas_per_system=5,
+                                         method="pipegcr", mmax=30, rtol=1e-8, maxit=12)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    ref = K.solve("pipegcr", aop, PC.JacobiPC(aop), c["b"], prm=K.Params(mmax=30, rtol=1e-8, maxit=12))
+    rho = ref.rho()
+    assert ref.breakdowns == 0
+    assert len(hists[0]) == len(rho) == 13
+    assert np.allclose(hists[0][:, 0], rho, rtol=1e-10, atol=0.0)
 
 
 def test_grouped_jacobi_2d_and_3d(ctx):
@@ -110,27 +144,30 @@ def test_grouped_nonzero_initial_guess_and_restart_truncation(ctx):
         check_solve(h, info, ref, alts, rtol=1e-8)
 
 
-def test_grouped_headline_regime_32cube(ctx):
+@pytest.mark.parametrize("method", ["pipefcg", "pipegcr"])
+def test_grouped_headline_regime_32cube(ctx, method):
     """The 32^3 headline case (contrast 1e6, 4 inner FP64 Jacobi-PCG, nu_max =
     30, rtol 1e-8, residual-replacement restarts) on the grouped kernel with the
     automatic CTA count, against the stored oracle envelope."""
     from paper_1511_07226_gb300 import pfk
     from tests import _oracle_pool as P
     from tests._headline_cases import CASES
-    if P.load_stored("pipefcg_32") is None:
+    name = f"{method}_32"
+    if P.load_stored(name) is None:
         pytest.skip("no stored envelope for these inputs")
-    cs = CASES["pipefcg_32"]
+    cs = CASES[name]
     c = P.problem(cs["problem"])
     prm = cs["prm"]
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
     xs, infos, hists = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4,
-                                         history=prm["maxit"] + 400, mmax=30, rtol=1e-8, maxit=prm["maxit"],
-                                         max_restarts=prm["max_restarts"])
+                                         history=prm["maxit"] + 400, method=method, mmax=30, rtol=1e-8,
+                                         maxit=prm["maxit"], max_restarts=prm["max_restarts"])
     ref, alts = P.envelope_runs(cs["problem"], cs["method"], cs["pc"], prm, orders=cs["orders"], big=cs["big"],
-                              stored="pipefcg_32")()
+                                stored=name)()
     s = check_solve(hists[0], infos[0], ref, alts, rtol=1e-8, check_restarts=True)
     assert s["prefix"] >= 10, s
-    assert infos[0]["status_name"] == "ok"
+    if ref.status == "converged" and all(a.status == "converged" for a in alts):
+        assert infos[0]["status_name"] == "ok"
 
 
 def test_grouped_barrier_timeout_is_reported(ctx):
@@ -148,30 +185,32 @@ def test_grouped_barrier_timeout_is_reported(ctx):
 
 
 def test_server_grouped_requests_bitwise_and_oracle(ctx):
-    """Requests served together through the grouped path equal, bit for bit,
-    the same requests solved alone by pfk_solve_grouped; a PIPEGCR request in
-    the same stream goes to a whole-GPU worker and equals pfk_solve alone; one
-    served grouped request is also checked against the oracle's envelope."""
+    """Requests served together through the grouped path (PIPEFCG and PIPEGCR)
+    equal, bit for bit, the same requests solved alone by pfk_solve_grouped; a
+    PIPEFGMRES request in the same stream goes to a whole-GPU worker and equals
+    pfk_solve alone; one served grouped request is also checked against the
+    oracle's envelope."""
     from paper_1511_07226_gb300 import pfk
     cs = [_cube(d, 90 + j) for j, d in enumerate([(24, 24, 24), (16, 16, 16), (20, 18, 22), (12, 30, 14)])]
+    meths = ["pipefcg", "pipegcr", "pipefcg", "pipegcr"]
     kw = dict(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50)
     srv = pfk.Server(ctx, workers=2)
     try:
-        tickets = [srv.submit(c["dims"], c["eta"], c["b"], **kw) for c in cs]
-        tg = srv.submit(cs[1]["dims"], cs[1]["eta"], cs[1]["b"], method="pipegcr", **kw)
+        tickets = [srv.submit(c["dims"], c["eta"], c["b"], method=m, **kw) for c, m in zip(cs, meths)]
+        tg = srv.submit(cs[1]["dims"], cs[1]["eta"], cs[1]["b"], method="pipefgmres", sigma=1.0, **kw)
         served = [srv.poll(t) for t in tickets]
         xg, ig, _ = srv.poll(tg)
     finally:
         srv.close()
-    for c, (x, info, lat) in zip(cs, served):
+    for c, m, (x, info, lat) in zip(cs, meths, served):
         op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
-        x1, i1, _ = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, **kw)
+        x1, i1, _ = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, method=m, **kw)
         assert np.array_equal(x, x1[0])
         assert info["iterations"] == i1[0]["iterations"] and info["restarts"] == i1[0]["restarts"]
         assert info["pass_launches"] == i1[0]["pass_launches"] >= 1
     op = pfk.Operator.stencil(ctx, cs[1]["dims"], cs[1]["eta"])
     pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
-    x1, i1, _ = pfk.solve(ctx, op, pc, cs[1]["b"], method="pipegcr", **kw)
+    x1, i1, _ = pfk.solve(ctx, op, pc, cs[1]["b"], method="pipefgmres", sigma=1.0, **kw)
     assert np.array_equal(xg, x1) and ig["iterations"] == i1["iterations"]
     # the served solution of the first request against the oracle's
     c = cs[0]

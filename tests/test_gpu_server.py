@@ -1,6 +1,8 @@
 """The continuous-batching server (pfk_server_*): every served result is bit for
-bit the result of the same request solved alone through pfk_solve, whatever
-else runs concurrently; admission, queue limit and ticket handling."""
+bit the result of the same request solved alone -- through pfk_solve_grouped
+for the small PIPEFCG / PIPEGCR requests the server advances on the grouped
+kernel, through pfk_solve for the rest -- whatever else runs concurrently;
+admission, queue limit and ticket handling."""
 import time
 
 import numpy as np
@@ -29,9 +31,22 @@ def _requests(count, lo=12, hi=36):
     return out
 
 
-def _alone(ctx, c, method):
+GROUP_MAX_N = 262144   # the server's default bound of grouped requests
+
+
+def _grouped(c, method, group_max_n=0):
+    """Whether a default server runs this request on the grouped kernel."""
+    bound = GROUP_MAX_N if group_max_n == 0 else group_max_n
+    return method in ("pipefcg", "pipegcr") and c["b"].size <= bound
+
+
+def _alone(ctx, c, method, group_max_n=0):
     from paper_1511_07226_gb300 import pfk
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    if _grouped(c, method, group_max_n):
+        xs, infos, _ = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, method=method,
+                                         **KW)
+        return xs[0], infos[0]
     pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
     x, info, _ = pfk.solve(ctx, op, pc, c["b"], method=method, **KW)
     return x, info
@@ -59,10 +74,11 @@ def test_served_results_equal_solves_alone(ctx, workers):
 
 def test_tiny_budget_admits_one_at_a_time_in_order(ctx):
     """With a budget below any request's estimate, a request is admitted only
-    when nothing else is active: requests finish in arrival order."""
+    when nothing else is active: requests finish in arrival order (all on the
+    workers: the arrival order holds within each admission path)."""
     from paper_1511_07226_gb300 import pfk
     reqs = _requests(6, 16, 28)
-    srv = pfk.Server(ctx, workers=4, memory_budget=1)
+    srv = pfk.Server(ctx, workers=4, memory_budget=1, group_max_n=-1)
     t0 = []
     tickets = []
     for r, c in reqs:
@@ -149,7 +165,7 @@ def test_smallest_first_order(ctx):
     reqs = _requests(6, 14, 30)
     big = W.request_problem(dict(side=40, log_contrast=4.0, method=0, item_id=777), ell=4.0)
     reqs = [(dict(side=40, method=0), big)] + reqs
-    srv = pfk.Server(ctx, workers=1, memory_budget=1, order="smallest_first")
+    srv = pfk.Server(ctx, workers=1, memory_budget=1, order="smallest_first", group_max_n=-1)
     t0, tickets = [], []
     for r, c in reqs:
         t0.append(time.perf_counter())
@@ -160,6 +176,27 @@ def test_smallest_first_order(ctx):
     completion = sorted(range(len(reqs)), key=lambda j: done[j])
     expected = [0] + sorted(range(1, len(reqs)), key=lambda j: (reqs[j][0]["side"], j))
     assert completion == expected, (completion, expected)
+    for (r, c), (x, info, _) in zip(reqs, results):
+        xa, ia = _alone(ctx, c, METHOD_OF[r["method"]], group_max_n=-1)
+        assert info["status_name"] == ia["status_name"] == "ok"
+        assert np.array_equal(x, xa)
+
+
+def test_tiny_budget_grouped_requests_one_at_a_time(ctx):
+    """The grouped path under the same tiny budget: grouped requests are
+    admitted one at a time in arrival order and each equals its grouped solve
+    alone."""
+    from paper_1511_07226_gb300 import pfk
+    reqs = [(r, c) for r, c in _requests(12, 14, 26) if METHOD_OF[r["method"]] != "pipefgmres"][:5]
+    srv = pfk.Server(ctx, workers=1, memory_budget=1)
+    t0, tickets = [], []
+    for r, c in reqs:
+        t0.append(time.perf_counter())
+        tickets.append(srv.submit(c["dims"], c["eta"], c["b"], method=METHOD_OF[r["method"]], **KW))
+    results = [srv.poll(t) for t in tickets]
+    srv.close()
+    done = [ts + lat / 1e3 for ts, (_, _, lat) in zip(t0, results)]
+    assert all(b >= a - 2e-3 for a, b in zip(done, done[1:])), np.diff(done)
     for (r, c), (x, info, _) in zip(reqs, results):
         xa, ia = _alone(ctx, c, METHOD_OF[r["method"]])
         assert info["status_name"] == ia["status_name"] == "ok"
@@ -203,8 +240,13 @@ def test_served_results_match_oracle(ctx, method):
     # the served history is that of the same solve alone (bitwise, tested
     # above); the alone run provides it
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
-    pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
-    xa, ia, hist = pfk.solve(ctx, op, pc, c["b"], method=method, sigma=1.0, history=4000, **KW)
+    if _grouped(c, method):
+        xs, ias, hs = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, method=method,
+                                        history=4000, **KW)
+        xa, ia, hist = xs[0], ias[0], hs[0]
+    else:
+        pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
+        xa, ia, hist = pfk.solve(ctx, op, pc, c["b"], method=method, sigma=1.0, history=4000, **KW)
     assert np.array_equal(x, xa) and info["iterations"] == ia["iterations"]
     aop = O.StencilOperator(c["dims"], c["eta"])
     prm = K.Params(mmax=30, rtol=1e-8, maxit=3000, sigma=1.0)
