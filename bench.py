@@ -794,7 +794,7 @@ def extra_fgmres256(ctx, dev, args) -> dict:
     return out
 
 
-GROUP_MAX_N = 262144   # the server's default: requests up to 64^3 unknowns run grouped when eligible
+GROUP_MAX_N = 110592   # the server's default: requests up to 48^3 unknowns run grouped when eligible
 
 
 def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo", group_max_n=0) -> dict:
@@ -866,14 +866,14 @@ def extra_serve(ctx, dev, args) -> dict:
 
 def grouped_fp64_per_unknown_iteration(nu: int, inner: int = 4) -> float:
     """FP64 instructions (DFMA / DMUL / DADD, one each) per unknown of one
-    PIPEFCG iteration on the grouped kernel, from its source: the pass 5 nu + 9
-    (four MAXPY FMAs and one window-dot FMA per window slot; the x, r, u, w
-    advance, t = w - r and four dot FMAs), the 7-point operator with its
-    advection terms 13, and `inner` Jacobi-PCG iterations 17 + 20 (inner - 1)
-    + 2 (first residual, dot and search direction with s = A p; per further
-    iteration the r, x and p updates, two dots and s = A p; the last x update
-    and m = u + x)."""
-    return 5.0 * nu + 9.0 + 13.0 + 17.0 + 20.0 * (inner - 1) + 2.0
+    PIPEFCG iteration on the grouped kernel, from its source, for a diffusion
+    operator: the pass 5 nu + 9 (four MAXPY FMAs and one window-dot FMA per
+    window slot; the x, r, u, w advance, t = w - r and four dot FMAs), the
+    7-point operator 7, and `inner` Jacobi-PCG iterations 11 + 14 (inner - 1)
+    + 2 (first residual dot, search direction and s = A p with its dot; per
+    further iteration the r, x and p updates, two dots and s = A p; the last
+    x update and m = u + x)."""
+    return 5.0 * nu + 9.0 + 7.0 + 11.0 + 14.0 * (inner - 1) + 2.0
 
 
 def extra_grouped(ctx, dev, args) -> dict:

@@ -437,7 +437,7 @@ typedef struct {
   int32_t group_max_n;     /* requests of at most this many unknowns that the grouped
                               kernel can run (pfk_solve_grouped: stencil, PIPEFCG or
                               PIPEGCR, NONE / JACOBI / FP64 INNER_PCG) are advanced together on
-                              it; 0 = 262,144 (64^3), < 0 = never */
+                              it; 0 = 110,592 (48^3), < 0 = never */
   int32_t group_ctas;      /* CTAs per grouped request, as pfk_solve_grouped's
                               ctas_per_system; 0 = automatic */
   int32_t reserved;        /* 0 */

@@ -40,6 +40,7 @@ struct BatchSys {
   const float* dinv32;
   double a0, a1, a2;
   int u0, u1, u2;
+  int adv;         // any advection weight non-zero
   const double* b;
   double* x;
   double* ws;      // r, u, w, m, n, t, tmp, then rings p, s, q, z of mmax+1 slots
@@ -103,6 +104,20 @@ template <typename V, typename C>
 __device__ __forceinline__ V sys_row(const BatchSys& S, const C* d, const C* kx, const C* ky, const C* kz,
                                      const V* m, int64_t c, int i, int j, int k) {
   const int64_t sxy = (int64_t)S.nx * S.ny;
+  if (!S.adv) {
+    // pure diffusion: the same products without the zero advection weights
+    // (adding +0 to a coefficient changes nothing)
+    V acc = (V)d[c] * m[c];
+    if (i > 0) acc = fma(-(V)kx[c - 1], m[c - 1], acc);
+    if (i < S.nx - 1) acc = fma(-(V)kx[c], m[c + 1], acc);
+    if (j > 0) acc = fma(-(V)ky[c - S.nx], m[c - S.nx], acc);
+    if (j < S.ny - 1) acc = fma(-(V)ky[c], m[c + S.nx], acc);
+    if (S.ndim == 3) {
+      if (k > 0) acc = fma(-(V)kz[c - sxy], m[c - sxy], acc);
+      if (k < S.nz - 1) acc = fma(-(V)kz[c], m[c + sxy], acc);
+    }
+    return acc;
+  }
   const V a0 = (V)S.a0, a1 = (V)S.a1, a2 = (V)S.a2;
   V acc = (V)d[c] * m[c];
   if (i > 0) acc = fma(-((V)kx[c - 1] + (S.u0 == -1 ? a0 : V(0))), m[c - 1], acc);
@@ -715,6 +730,7 @@ extern "C" pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_op
     S.d32 = op->d32; S.kx32 = op->kx32; S.ky32 = op->ky32; S.kz32 = op->kz32; S.dinv32 = op->dinv32;
     S.a0 = op->adv[0]; S.a1 = op->adv[1]; S.a2 = op->adv[2];
     S.u0 = op->upw[0]; S.u1 = op->upw[1]; S.u2 = op->upw[2];
+    S.adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
     S.ws = dws + wsoff[j];
     S.pcws = dpc + pcoff[j];
     S.hist = hcap ? dhist + (int64_t)j * hcap * 4 : nullptr;

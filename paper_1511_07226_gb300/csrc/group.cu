@@ -86,7 +86,9 @@ struct GrpSys {
   const double* dinv;
   double a0, a1, a2;
   int u0, u1, u2;
+  int adv;            // any advection weight non-zero
   int nblk;           // CTAs of the group
+  int pad0;
   const double* b;
   double* x;
   double* ws;         // r, u, w, m, n, t, tmp, then rings P, S, Q, Z of mmax + 1 slots
@@ -225,6 +227,20 @@ __device__ void grp_sum(const GrpSys& S, GrpCta* g, const double (&v)[ND], doubl
 // launch, so its loads go to L2 (never a stale L1 line).
 __device__ __forceinline__ double grp_row(const GrpSys& S, const double* m, int64_t c, int i, int j, int k) {
   const int64_t sxy = (int64_t)S.nx * S.ny;
+  if (!S.adv) {
+    // pure diffusion: the same products without the zero advection weights
+    // (adding +0.0 to a coefficient changes nothing)
+    double acc = S.d[c] * __ldcg(m + c);
+    if (i > 0) acc = fma(-S.kx[c - 1], __ldcg(m + c - 1), acc);
+    if (i < S.nx - 1) acc = fma(-S.kx[c], __ldcg(m + c + 1), acc);
+    if (j > 0) acc = fma(-S.ky[c - S.nx], __ldcg(m + c - S.nx), acc);
+    if (j < S.ny - 1) acc = fma(-S.ky[c], __ldcg(m + c + S.nx), acc);
+    if (S.ndim == 3) {
+      if (k > 0) acc = fma(-S.kz[c - sxy], __ldcg(m + c - sxy), acc);
+      if (k < S.nz - 1) acc = fma(-S.kz[c], __ldcg(m + c + sxy), acc);
+    }
+    return acc;
+  }
   double acc = S.d[c] * __ldcg(m + c);
   if (i > 0) acc = fma(-(S.kx[c - 1] + (S.u0 == -1 ? S.a0 : 0.0)), __ldcg(m + c - 1), acc);
   if (i < S.nx - 1) acc = fma(-(S.kx[c] + (S.u0 == 1 ? S.a0 : 0.0)), __ldcg(m + c + 1), acc);
@@ -1043,6 +1059,7 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
   S.d = op->d; S.kx = op->kx; S.ky = op->ky; S.kz = op->kz; S.dinv = op->dinv;
   S.a0 = op->adv[0]; S.a1 = op->adv[1]; S.a2 = op->adv[2];
   S.u0 = op->upw[0]; S.u1 = op->upw[1]; S.u2 = op->upw[2];
+  S.adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
   S.nblk = nblk;
   S.b = b_dev;
   S.x = x_dev;

@@ -369,7 +369,7 @@ pfk_status pfk_server_create(pfk_context* ctx, const pfk_server_params* params, 
   }
   srv->order = params ? params->order : PFK_SERVE_FIFO;
   const int32_t gmax = params ? params->group_max_n : 0;
-  srv->group_max_n = gmax == 0 ? 262144 : (gmax < 0 ? 0 : gmax);
+  srv->group_max_n = gmax == 0 ? 110592 : (gmax < 0 ? 0 : gmax);
   srv->group_ctas = params ? params->group_ctas : 0;
   if (srv->group_ctas < 0 || srv->group_ctas > 64) {
     delete srv;

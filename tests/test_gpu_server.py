@@ -31,7 +31,7 @@ def _requests(count, lo=12, hi=36):
     return out
 
 
-GROUP_MAX_N = 262144   # the server's default bound of grouped requests
+GROUP_MAX_N = 110592   # the server's default bound of grouped requests
 
 
 def _grouped(c, method, group_max_n=0):
