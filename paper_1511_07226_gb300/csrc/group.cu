@@ -210,7 +210,8 @@ __device__ void grp_sum(const GrpSys& S, GrpCta* g, const double (&v)[ND], doubl
   __syncthreads();
 }
 
-// The CTA's cells (contiguous: whole x-rows).
+// The CTA's cells (contiguous: whole x-rows).  Call sites unroll these loops
+// (more loads in flight per thread; the accumulation order is unchanged).
 #define GRP_ELEMS(S, g, e)                                                                          \
   for (int64_t e = (g)->row_lo * (S).nx + threadIdx.x, e_end_ = (g)->row_hi * (S).nx; e < e_end_;  \
        e += kGrpThreads)
@@ -257,6 +258,7 @@ __device__ __forceinline__ double grp_row(const GrpSys& S, const double* m, int6
 // every CTA of the group (the caller passed a system barrier since it was
 // last written).
 __device__ void grp_apply(const GrpSys& S, GrpCta* g, const double* m, double* y, const double* bsub) {
+  #pragma unroll 2
   GRP_ROWS(S, g, c, i, j, k) {
     const double v = grp_row(S, m, c, i, j, k);
     y[c] = bsub ? bsub[c] - v : v;
@@ -272,6 +274,7 @@ __device__ void grp_apply(const GrpSys& S, GrpCta* g, const double* m, double* y
 __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out, const double* add, double* s_red) {
   const GrpParams& P = S.P;
   if (P.pc_kind != PFK_PC_INNER_PCG) {
+    #pragma unroll 4
     GRP_ELEMS(S, g, e) {
       // B(v) = D^-1 v and add + B(v): two roundings (no fused multiply-add)
       const double y = P.pc_kind == PFK_PC_JACOBI ? __dmul_rn(S.dinv[e], v[e]) : v[e];
@@ -290,6 +293,7 @@ __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out,
   {
     // r_0 = v; gamma_0 = <D^-1 r_0, r_0>
     double acc[1] = {0.0};
+    #pragma unroll 4
     GRP_ELEMS(S, g, e) {
       const double rv = v[e];
       r[e] = rv;
@@ -304,9 +308,11 @@ __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out,
   }
   if (g->last_x > 0) {
     // p_0 = D^-1 r_0, s_0 = A p_0, eta_0 = <s_0, p_0>
+    #pragma unroll 4
     GRP_ELEMS(S, g, e) p[e] = dinv[e] * r[e];
     grp_barrier(S, g);
     double acc[1] = {0.0};
+    #pragma unroll 2
     GRP_ROWS(S, g, c, i, j, k) {
       const double sv = grp_row(S, p, c, i, j, k);
       s[c] = sv;
@@ -325,6 +331,7 @@ __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out,
       // r_i = r_{i-1} - alpha_{i-1} s_{i-1}; gamma_i
       const double al = g->palpha[it - 1];
       double acc[1] = {0.0};
+      #pragma unroll 4
       GRP_ELEMS(S, g, e) {
         const double rv = r[e] - al * s[e];
         r[e] = rv;
@@ -347,6 +354,7 @@ __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out,
       const double al = g->palpha[it - 1];
       const double be = g->pbeta;
       const bool do_p = it < g->last_x;
+      #pragma unroll 4
       GRP_ELEMS(S, g, e) {
         const double po = p[e];
         x[e] = (it == 1 ? 0.0 : x[e]) + al * po;
@@ -361,6 +369,7 @@ __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out,
     {
       // s_i = A p_i, eta_i
       double acc[1] = {0.0};
+      #pragma unroll 2
       GRP_ROWS(S, g, c, i, j, k) {
         const double sv = grp_row(S, p, c, i, j, k);
         s[c] = sv;
@@ -376,6 +385,7 @@ __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out,
   }
   const int last_x = g->last_x;
   const double al = g->palpha[kk - 1];
+  #pragma unroll 4
   GRP_ELEMS(S, g, e) {
     double y;
     if (last_x == 0) y = 0.0;
@@ -612,6 +622,7 @@ __device__ void grp_gcr_advance(const GrpSys& S, GrpCta* g) {
   }
   __syncthreads();
   const size_t coff = (size_t)(iprev % slots) * (size_t)n;
+  #pragma unroll 4
   GRP_ELEMS(S, g, e) {
     const double u0 = vu[e];
     double p = u0, sv = vw[e], q = vm[e];
@@ -650,6 +661,7 @@ __device__ void grp_gcr_dots(const GrpSys& S, GrpCta* g, double* smem) {
   const double* Sr = S.ws + 7 * n + (int64_t)slots * n;
   const int i = st->i + 1;
   const int nu = nu_window(i, S.P.mmax, S.P.truncation);
+  #pragma unroll 2
   GRP_ROWS(S, g, c, ii, j, k) {
     const double wv = grp_row(S, vu, c, ii, j, k);
     vw[c] = wv;
@@ -727,6 +739,7 @@ __device__ void grp_fill(const GrpSys& S, GrpCta* g, double* smem) {
   // Alg. 8: gamma_0 = <u_0, r_0>, eta_0 = delta_0 = <u_0, w_0>;
   // Alg. 11: gamma_0 = <r_0, s_0>, eta_0 = <s_0, s_0>; and ||r_0||^2
   double acc[3] = {0.0, 0.0, 0.0};
+  #pragma unroll 4
   GRP_ELEMS(S, g, e) {
     const double a = gcr ? vw[e] : vu[e];
     acc[0] = fma(a, vr[e], acc[0]);
@@ -766,6 +779,7 @@ __device__ void grp_true_residual(const GrpSys& S, GrpCta* g, double* smem) {
   double* tmp = S.ws + 6 * S.n;
   grp_apply(S, g, S.x, tmp, S.b);
   double acc[1] = {0.0};
+  #pragma unroll 4
   GRP_ELEMS(S, g, e) acc[0] = fma(tmp[e], tmp[e], acc[0]);
   grp_sum<1>(S, g, acc, smem);
   if (threadIdx.x == 0) g->red[0] = sqrt(g->red[0]);
