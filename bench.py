@@ -827,7 +827,7 @@ def _serve_replay(ctx, reqs, probs, workers, rate_scale=1.0, order="fifo", group
     unk_its = float(sum(int(np.prod(p["dims"])) * i for p, i in zip(probs, its)))
     unknowns = int(sum(r["side"] ** 3 for r in reqs))
     gmax = GROUP_MAX_N if group_max_n == 0 else max(group_max_n, 0)
-    grouped = [j for j, r in enumerate(reqs) if meth[r["method"]] in ("pipefcg", "pipegcr") and r["side"] ** 3 <= gmax]
+    grouped = [j for j, r in enumerate(reqs) if r["side"] ** 3 <= gmax]
     small = [j for j, r in enumerate(reqs) if r["side"] ** 3 <= GROUP_MAX_N]
     return {"workers": workers, "order": order, "group_max_n": gmax, "requests": len(reqs),
             "grouped_requests": len(grouped),

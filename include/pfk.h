@@ -371,8 +371,10 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
                              const pfk_solve_params* params, const double* const* b, double* const* x,
                              int ptrs_on_device, int block_threads, pfk_solve_info* infos);
 
-/* Solves nsys independent stencil systems with PIPEFCG (Alg. 8) or PIPEGCR
- * (Alg. 11) on the grouped persistent kernel: each system is advanced by its own group of CTAs
+/* Solves nsys independent stencil systems with PIPEFCG (Alg. 8), PIPEGCR
+ * (Alg. 11) or PIPEFGMRES (Alg. 15, constant shift sigma: params.sigma, or
+ * NaN for 10 power iterations on v -> A B(v)) on the grouped persistent
+ * kernel: each system is advanced by its own group of CTAs
  * (a contiguous range of x-rows per CTA) and the active systems share
  * cooperative launches of a few iterations each, between which finished
  * systems leave and queued ones (in the given order) join.  Within a group
@@ -384,7 +386,7 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
  * pfk_solve.
  *  - ops[j]: matrix-free stencil operators; pc: NONE, JACOBI or INNER_PCG in
  *    FP64 (1..64 inner iterations), the same description for all systems.
- *  - params: method PFK_PIPEFCG or PFK_PIPEGCR; graph_iters, profile and persistent are
+ *  - params: method PFK_PIPEFCG, PFK_PIPEGCR or PFK_PIPEFGMRES; graph_iters, profile and persistent are
  *    ignored; barrier_timeout_us as for pfk_solve; history (if set) holds
  *    nsys consecutive blocks of history_capacity entries.
  *  - b[j], x[j]: host (ptrs_on_device = 0) or device (1) vectors of length
@@ -435,8 +437,9 @@ typedef struct {
   int64_t memory_budget;   /* device bytes for active solves; 0 = 80 % of free memory */
   int32_t order;           /* pfk_serve_order; 0 = FIFO */
   int32_t group_max_n;     /* requests of at most this many unknowns that the grouped
-                              kernel can run (pfk_solve_grouped: stencil, PIPEFCG or
-                              PIPEGCR, NONE / JACOBI / FP64 INNER_PCG) are advanced together on
+                              kernel can run (pfk_solve_grouped: stencil, PIPEFCG,
+                              PIPEGCR or PIPEFGMRES, NONE / JACOBI / FP64 INNER_PCG) are
+                              advanced together on
                               it; 0 = 110,592 (48^3), < 0 = never */
   int32_t group_ctas;      /* CTAs per grouped request, as pfk_solve_grouped's
                               ctas_per_system; 0 = automatic */

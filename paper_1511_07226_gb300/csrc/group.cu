@@ -1,5 +1,6 @@
-// Grouped persistent PIPEFCG / PIPEGCR: several stencil systems advanced
-// together by one cooperative launch, each system by its own group of CTAs.
+// Grouped persistent PIPEFCG / PIPEGCR / PIPEFGMRES: several stencil systems
+// advanced together by one cooperative launch, each system by its own group
+// of CTAs.
 //
 // A system of n cells belongs to a group of C CTAs (by default about 4,096
 // cells per CTA, at most kGrpMaxCtas); the CTA of rank q owns a contiguous
@@ -11,7 +12,10 @@
 // Jacobi, or k inner Jacobi-PCG iterations, Alg. 3, in FP64) and the
 // operator.  PIPEGCR (Alg. 11) splits the pass in two: the deferred MAXPYs
 // with the advance of x, r, u, then w_i = A u_i with the dots gamma_i =
-// <r_i, w_i>, delta_i = <w_i, w_i>, ||r_i||^2 and <w_i, s_k>.  A reduction writes one partial row per CTA; the CTAs meet at the
+// <r_i, w_i>, delta_i = <w_i, w_i>, ||r_i||^2 and <w_i, s_k>.  PIPEFGMRES
+// (Alg. 15) forms p_k, u_k, zbar_k and the dots of Hessenberg column k in one
+// pass; every CTA keeps the Givens rotations, and a restart cycle ends with
+// the least-squares solution and x = x_0 + U y.  A reduction writes one partial row per CTA; the CTAs meet at the
 // system's own barrier (an arrival counter and a generation word of that
 // system, with bounded waits) and every CTA sums the rows in rank order, so
 // all CTAs of the group hold bitwise the same scalars and run the scalar
@@ -55,6 +59,7 @@ struct GrpParams {
   double rtol, atol;
   int pc_kind, pc_inner;
   long long bar_timeout_ns;   // bound of each barrier wait (<= 0: no wait allowed)
+  double sigma;               // PIPEFGMRES shift; NaN: estimated at the start
 };
 
 // Barrier words of one system (reset by the host at admission).
@@ -72,7 +77,12 @@ struct GrpState {
   double alpha, gamma, delta, eta, target, rho0, rho, bnorm, goal, rtrue;
   double beta[PFK_MAX_MMAX];
   double eta_ring[PFK_MAX_MMAX + 1];
-  double pad1;
+  // PIPEFGMRES: the shift, and the current restart cycle's Givens rotations,
+  // rotated right-hand side g and previous Hessenberg column (hbar and h)
+  double sigma, gm_inv;
+  double gm_cs[PFK_MAX_MMAX], gm_sn[PFK_MAX_MMAX], gm_g[PFK_MAX_MMAX + 1];
+  double gm_hb[PFK_MAX_MMAX + 1], gm_h[PFK_MAX_MMAX + 1];
+  int gm_k, gm_ncols;      // column the next pass forms; valid columns of the cycle
 };
 static_assert(sizeof(GrpState) % 8 == 0, "GrpState is copied as 8-byte words");
 
@@ -94,6 +104,7 @@ struct GrpSys {
   double* ws;         // r, u, w, m, n, t, tmp, then rings P, S, Q, Z of mmax + 1 slots
   double* pcws;       // inner PCG: r, p, s, x
   double* part;       // [2][nblk][kGrpNd] partial rows
+  double* gm;         // PIPEFGMRES: rotated Hessenberg R [(m+1) x m], then y [m]
   double* hist;
   int hist_cap, pad;
   GrpParams P;
@@ -110,6 +121,9 @@ struct GrpCta {
   double pg, pbeta;              // inner PCG scalars
   double palpha[kGrpMaxInner];
   double s_beta[kGrpNW];
+  double s_h[kGrpNW];            // PIPEFGMRES: h_{j,k-1} of the pass
+  double s_y[kGrpNW];            // PIPEFGMRES: least-squares solution of the cycle
+  double s_col[kGrpNW + 1];      // PIPEFGMRES: the column being rotated
   double s_tot[kGrpNd];
   size_t s_off[kGrpNW];
   int last_x, par, rank, nblk, abort, pad;
@@ -720,6 +734,283 @@ __device__ void grp_gcr_dots(const GrpSys& S, GrpCta* g, double* smem) {
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// PIPEFGMRES (Alg. 15, constant shift sigma, eq. pipefgmresz).  Vectors: r at
+// ws, qbar at ws + n, wbar at ws + 2n, the true-residual scratch at ws + 6n,
+// then the cycle's p_j, u_j and zbar_j (m each).  Every CTA keeps the
+// rotations, g and the last column itself (identical in all CTAs); rank 0
+// writes the rotated columns R for the end of the cycle.
+// ---------------------------------------------------------------------------
+
+// Column k of H from its dots (hb[j] = <p_j, zbar_k>, j <= k; zz =
+// ||zbar_k||^2): hbar and h = hbar + sigma e_k, t = zz - sum hbar^2 (norm
+// breakdown if t < 0), hbar_{k+1,k} = sqrt(t), the previous rotations and a
+// new one, the least-squares residual estimate |g_{k+1}| and the status.
+// Thread 0.
+__device__ void grp_gm_column(const GrpSys& S, GrpCta* g, int k, const double* hb, double zz) {
+  GrpState* st = &g->st;
+  const int m = S.P.mmax;
+  double tsum = 0.0;
+  for (int j = 0; j <= k; ++j) {
+    st->gm_hb[j] = hb[j];
+    st->gm_h[j] = hb[j];
+    tsum += hb[j] * hb[j];
+  }
+  st->gm_h[k] = hb[k] + st->sigma;
+  const double t = zz - tsum;
+  if (!(t >= 0.0)) {
+    st->i = k + 1;     // columns 0 .. k-1 are valid
+    st->gm_ncols = k;
+    st->status = isfinite(t) ? kBreakdown : kNonFinite;
+    return;
+  }
+  const double hsub = sqrt(t);
+  st->gm_hb[k + 1] = hsub;
+  st->gm_h[k + 1] = hsub;
+  st->it += 1;
+  st->gm_ncols = k + 1;
+  st->i = k + 1;
+  double* col = g->s_col;
+  for (int j = 0; j <= k + 1; ++j) col[j] = st->gm_h[j];
+  for (int j = 0; j < k; ++j) {
+    const double a = col[j], b = col[j + 1];
+    col[j] = st->gm_cs[j] * a + st->gm_sn[j] * b;
+    col[j + 1] = -st->gm_sn[j] * a + st->gm_cs[j] * b;
+  }
+  const double a = col[k], b = col[k + 1];
+  const double rr = hypot(a, b);
+  const double c = rr != 0.0 ? a / rr : 1.0, sn = rr != 0.0 ? b / rr : 0.0;
+  st->gm_cs[k] = c;
+  st->gm_sn[k] = sn;
+  col[k] = rr;
+  col[k + 1] = 0.0;
+  if (g->rank == 0)
+    for (int j = 0; j <= k + 1; ++j) S.gm[j * m + k] = col[j];
+  st->gm_g[k + 1] = -sn * st->gm_g[k];
+  st->gm_g[k] = c * st->gm_g[k];
+  const double est = fabs(st->gm_g[k + 1]);
+  st->rho = est;
+  grp_push_history(S, g, est, nan(""), t, hsub);
+  st->gm_inv = hsub != 0.0 ? 1.0 / hsub : 0.0;
+  st->gm_k = k + 1;
+  if (!isfinite(est)) st->status = kNonFinite;
+  else if (est <= st->target || t == 0.0) st->status = kConverged;
+  else if (k + 1 == m) st->status = kCycleEnd;
+  else if (st->it >= S.P.maxit) st->status = kMaxit;
+  else st->status = kRun;
+}
+
+// Cycle start: r_0 = b - A x_0 and beta = ||r_0|| (history, target,
+// convergence); if the cycle runs, p_0 = r_0 / beta, u_0 = B(p_0), zbar_0 =
+// A u_0 - sigma p_0 with the dots of column 0, and column 0.
+__device__ void grp_gm_fill(const GrpSys& S, GrpCta* g, double* smem) {
+  GrpState* st = &g->st;
+  const int64_t n = S.n;
+  const int m = S.P.mmax;
+  double* r = S.ws;
+  double* P0 = S.ws + 7 * n;
+  double* U0 = P0 + (int64_t)m * n;
+  double* Z0 = U0 + (int64_t)m * n;
+  grp_apply(S, g, S.x, r, S.b);
+  {
+    double acc[1] = {0.0};
+    GRP_ELEMS(S, g, e) acc[0] = fma(r[e], r[e], acc[0]);
+    grp_sum<1>(S, g, acc, smem);
+  }
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(g->red[0]);
+    if (!st->target_set) {
+      st->rho0 = beta;
+      st->target = fmax(S.P.rtol * beta, S.P.atol);
+      st->target_set = 1;
+    }
+    grp_push_history(S, g, beta, beta, nan(""), nan(""));
+    st->rho = beta;
+    st->i = 0;
+    st->gm_g[0] = beta;
+    st->gm_k = 0;
+    st->gm_ncols = 0;
+    st->gm_inv = beta != 0.0 ? 1.0 / beta : 0.0;
+    if (!isfinite(beta)) st->status = kNonFinite;
+    else if (beta <= st->target) st->status = kConverged;
+    else if (st->it >= S.P.maxit) st->status = kMaxit;
+    else st->status = kRun;
+  }
+  __syncthreads();
+  if (st->status != kRun) return;
+  const double inv = st->gm_inv;
+  GRP_ELEMS(S, g, e) P0[e] = r[e] * inv;
+  grp_pc(S, g, P0, U0, nullptr, smem);       // u_0 = B(p_0)
+  grp_apply(S, g, U0, Z0, nullptr);          // A u_0
+  const double sigma = st->sigma;
+  double acc[2] = {0.0, 0.0};
+#pragma unroll 4
+  GRP_ELEMS(S, g, e) {
+    const double pv = P0[e];
+    const double zv = fma(-sigma, pv, Z0[e]);
+    Z0[e] = zv;
+    acc[0] = fma(zv, zv, acc[0]);
+    acc[1] = fma(pv, zv, acc[1]);
+  }
+  grp_sum<2>(S, g, acc, smem);
+  if (threadIdx.x == 0) grp_gm_column(S, g, 0, &g->red[1], g->red[0]);
+  __syncthreads();
+}
+
+// Pass k >= 1: p_k = (zbar_{k-1} - sum_j hbar_{j,k-1} p_j) / hbar_{k,k-1},
+// u_k = (qbar - sum_j hbar_{j,k-1} u_j) / hbar_{k,k-1}, zbar_k = (wbar -
+// sum_j h_{j,k-1} zbar_j) / hbar_{k,k-1} (reciprocal multiply), with the dots
+// <p_j, zbar_k> (j <= k; the p_j read by the MAXPY transposed through shared
+// memory as in the PIPEFCG pass) and ||zbar_k||^2, then column k.
+__device__ void grp_gm_pass(const GrpSys& S, GrpCta* g, double* smem) {
+  constexpr int T = kGrpThreads;
+  GrpState* st = &g->st;
+  const int64_t n = S.n;
+  const int m = S.P.mmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = st->gm_k;
+  const double inv = st->gm_inv;
+  double* P = S.ws + 7 * n;
+  double* U = P + (int64_t)m * n;
+  double* Zb = U + (int64_t)m * n;
+  const double* qb = S.ws + n;
+  const double* wb = S.ws + 2 * n;
+  if (threadIdx.x < k) {
+    g->s_beta[threadIdx.x] = st->gm_hb[threadIdx.x];
+    g->s_h[threadIdx.x] = st->gm_h[threadIdx.x];
+  }
+  __syncthreads();
+  const size_t koff = (size_t)k * (size_t)n, km1 = (size_t)(k - 1) * (size_t)n;
+  double* s_sk = smem;
+  double* s_z = s_sk + kGrpNW * (T + 1);
+  double* s_red = s_z + T;
+  double* my = s_sk + threadIdx.x;
+  const double* wz = s_z + warp * 32;
+  const double* lrow = s_sk + lane * (T + 1) + warp * 32;
+  double gz = 0.0, gp = 0.0, gw = 0.0;
+  const int64_t e_lo = g->row_lo * S.nx, e_hi = g->row_hi * S.nx;
+  for (int64_t base = e_lo; base < e_hi; base += T) {
+    const int64_t e = base + threadIdx.x;
+    double zk = 0.0;
+    if (e < e_hi) {
+      double p = Zb[km1 + e], u = qb[e], z = wb[e];
+#pragma unroll 4
+      for (int j = 0; j < k; ++j) {
+        const size_t o = (size_t)j * (size_t)n + e;
+        const double pj = P[o];
+        p = fma(-g->s_beta[j], pj, p);
+        u = fma(-g->s_beta[j], U[o], u);
+        z = fma(-g->s_h[j], Zb[o], z);
+        my[j * (T + 1)] = pj;
+      }
+      p *= inv;
+      u *= inv;
+      zk = z * inv;
+      P[koff + e] = p;
+      U[koff + e] = u;
+      Zb[koff + e] = zk;
+      gz = fma(zk, zk, gz);
+      gp = fma(p, zk, gp);
+    } else {
+      for (int j = 0; j < k; ++j) my[j * (T + 1)] = 0.0;
+    }
+    s_z[threadIdx.x] = zk;
+    __syncwarp();
+    if (lane < k) {
+      double c = gw;
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) c = fma(wz[t], lrow[t], c);
+      gw = c;
+    }
+    __syncwarp();
+  }
+  const int nd = k + 2;     // ||zbar_k||^2, <p_j, zbar_k> for j = 0 .. k
+  {
+    const double a0 = warp_sum(gz), a1 = warp_sum(gp);
+    if (lane == 0) {
+      s_red[warp * nd + 0] = a0;
+      s_red[warp * nd + 1 + k] = a1;
+    }
+    if (lane < k) s_red[warp * nd + 1 + lane] = gw;
+  }
+  __syncthreads();
+  grp_combine_row(S, g, nd, s_red);
+  if (threadIdx.x == 0) grp_gm_column(S, g, k, g->s_tot + 1, g->s_tot[0]);
+  __syncthreads();
+}
+
+// qbar = B(zbar_k), wbar = A qbar (the next pass's inputs).
+__device__ void grp_gm_precondition(const GrpSys& S, GrpCta* g, double* smem, int k) {
+  const int64_t n = S.n;
+  const int m = S.P.mmax;
+  const double* Zk = S.ws + 7 * n + 2 * (int64_t)m * n + (int64_t)k * n;
+  double* qb = S.ws + n;
+  double* wb = S.ws + 2 * n;
+  grp_pc(S, g, Zk, qb, nullptr, smem);
+  grp_apply(S, g, qb, wb, nullptr);
+}
+
+// End of a cycle: back substitution R y = g on the valid columns (every CTA,
+// from the columns rank 0 wrote), x = x_0 + sum_j y_j u_j; ends at the
+// system's barrier (x then feeds an operator).
+__device__ void grp_gm_end_cycle(const GrpSys& S, GrpCta* g) {
+  GrpState* st = &g->st;
+  const int nc = st->gm_ncols;
+  if (nc == 0) return;
+  const int m = S.P.mmax;
+  const int64_t n = S.n;
+  grp_barrier(S, g);
+  if (threadIdx.x == 0) {
+    for (int j = nc - 1; j >= 0; --j) {
+      double s = st->gm_g[j];
+      for (int l = j + 1; l < nc; ++l) s -= __ldcg(&S.gm[j * m + l]) * g->s_y[l];
+      g->s_y[j] = s / __ldcg(&S.gm[j * m + j]);
+    }
+  }
+  __syncthreads();
+  const double* U = S.ws + 7 * n + (int64_t)m * n;
+#pragma unroll 4
+  GRP_ELEMS(S, g, e) {
+    double v = S.x[e];
+    for (int j = 0; j < nc; ++j) v = fma(g->s_y[j], U[(size_t)j * (size_t)n + e], v);
+    S.x[e] = v;
+  }
+  grp_barrier(S, g);
+}
+
+// The shift sigma when none is given: 10 power iterations on v -> A B(v)
+// from v = b / ||b|| (sigma = ||A B(v)|| at the last step).
+__device__ void grp_gm_sigma(const GrpSys& S, GrpCta* g, double* smem) {
+  GrpState* st = &g->st;
+  if (!isnan(S.P.sigma)) {
+    if (threadIdx.x == 0) st->sigma = S.P.sigma;
+    __syncthreads();
+    return;
+  }
+  const int64_t n = S.n;
+  double* v = S.ws;
+  double* t = S.ws + 6 * n;
+  double* q = S.ws + n;
+  double nrm = st->bnorm;
+  {
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    GRP_ELEMS(S, g, e) v[e] = S.b[e] * inv;
+  }
+  for (int it = 0; it < 10; ++it) {
+    grp_pc(S, g, v, t, nullptr, smem);
+    grp_apply(S, g, t, q, nullptr);
+    double acc[1] = {0.0};
+    GRP_ELEMS(S, g, e) acc[0] = fma(q[e], q[e], acc[0]);
+    grp_sum<1>(S, g, acc, smem);
+    nrm = sqrt(g->red[0]);
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    GRP_ELEMS(S, g, e) v[e] = q[e] * inv;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->sigma = nrm;
+  __syncthreads();
+}
+
 // Pipeline fill (Alg. 8 / Alg. 11, before the loop) from the current x.
 __device__ void grp_fill(const GrpSys& S, GrpCta* g, double* smem) {
   GrpState* st = &g->st;
@@ -869,9 +1160,33 @@ __global__ void __launch_bounds__(kGrpThreads, 3)
       st->phase = kGFill;
     }
     __syncthreads();
+    if (S.P.method == PFK_PIPEFGMRES) grp_gm_sigma(S, &g, smem);
   }
   for (int step = 0; step < iters && st->phase != kGDone && !g.abort; ++step) {
     if (threadIdx.x == 0) st->steps += 1;
+    if (S.P.method == PFK_PIPEFGMRES) {
+      // a step: the cycle start with column 0, or pass k; then B and A for
+      // the next pass, or the end of the cycle
+      if (st->phase == kGFill) grp_gm_fill(S, &g, smem);
+      else grp_gm_pass(S, &g, smem);
+      if (st->status == kRun) {
+        grp_gm_precondition(S, &g, smem, st->gm_k - 1);
+        if (threadIdx.x == 0) st->phase = kGIter;
+        __syncthreads();
+        continue;
+      }
+      if (st->status != kNonFinite) grp_gm_end_cycle(S, &g);
+      if (st->status == kCycleEnd) {
+        if (threadIdx.x == 0) {
+          st->prev_bd = 0;
+          st->phase = kGFill;
+        }
+        __syncthreads();
+      } else {
+        grp_after_cycle(S, &g, smem);
+      }
+      continue;
+    }
     if (st->phase == kGFill) {
       grp_fill(S, &g, smem);
       if (threadIdx.x == 0 && st->status == kRun) st->phase = kGIter;
@@ -927,8 +1242,8 @@ size_t grp_smem_bytes() {
 
 bool group_method_eligible(const pfk_pc_desc* pcd, const pfk_solve_params* prm, const char** why) {
   const char* w = nullptr;
-  if (!prm || (prm->method != PFK_PIPEFCG && prm->method != PFK_PIPEGCR))
-    w = "the grouped solve runs PFK_PIPEFCG or PFK_PIPEGCR";
+  if (!prm || (prm->method != PFK_PIPEFCG && prm->method != PFK_PIPEGCR && prm->method != PFK_PIPEFGMRES))
+    w = "the grouped solve runs PFK_PIPEFCG, PFK_PIPEGCR or PFK_PIPEFGMRES";
   else if (prm->mmax < 1 || prm->mmax > PFK_MAX_MMAX) w = "mmax out of range";
   else if (pcd && !(pcd->kind == PFK_PC_NONE || pcd->kind == PFK_PC_JACOBI ||
                     (pcd->kind == PFK_PC_INNER_PCG && pcd->precision == PFK_FP64 && pcd->inner_iters >= 1 &&
@@ -1033,7 +1348,9 @@ bool GroupRunner::any_active() const { return m_->used_ctas > 0; }
 
 int64_t GroupRunner::workspace_bytes(int64_t n, int mmax, int nblk) {
   const int64_t slots = mmax + 1;
-  return (int64_t)sizeof(double) * ((7 + 4 * slots) * n + 4 * n + 2 * (int64_t)nblk * kGrpNd) + 256;
+  return (int64_t)sizeof(double) *
+             ((7 + 4 * slots) * n + 4 * n + 2 * (int64_t)nblk * kGrpNd + (int64_t)(mmax + 2) * mmax) +
+         256;
 }
 
 pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, const pfk_solve_params* prm,
@@ -1080,6 +1397,7 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
   S.ws = (double*)mem;
   S.pcws = S.ws + (7 + 4 * (int64_t)(prm->mmax + 1)) * n;
   S.part = S.pcws + 4 * n;
+  S.gm = S.part + 2 * (int64_t)nblk * kGrpNd;
   S.hist = hist_dev;
   S.hist_cap = hist_dev ? hist_cap : 0;
   GrpParams& P = S.P;
@@ -1089,6 +1407,7 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
   P.rtol = prm->rtol; P.atol = prm->atol;
   P.pc_kind = pcd ? pcd->kind : PFK_PC_NONE;
   P.pc_inner = pcd ? pcd->inner_iters : 0;
+  P.sigma = prm->sigma;
   P.bar_timeout_ns = prm->barrier_timeout_us == 0 ? 2000000000LL
                      : prm->barrier_timeout_us < 0 ? 0LL
                                                    : (long long)prm->barrier_timeout_us * 1000LL;
@@ -1098,6 +1417,7 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
   s0.phase = kGStart;
   s0.status = kRun;
   s0.rtrue = NAN;
+  s0.sigma = NAN;
   M.hsys[slot] = S;
   M.hstate[slot] = s0;
   PFK_CUDA(ctx, cudaMemcpyAsync(M.dsys + slot, &M.hsys[slot], sizeof(GrpSys), cudaMemcpyHostToDevice, M.st));

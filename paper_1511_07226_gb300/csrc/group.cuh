@@ -1,4 +1,4 @@
-// Grouped persistent PIPEFCG / PIPEGCR (group.cu): host interface used by the grouped
+// Grouped persistent PIPEFCG / PIPEGCR / PIPEFGMRES (group.cu): host interface used by the grouped
 // batch entry point and by the serving loop.
 #pragma once
 
@@ -6,9 +6,9 @@
 
 namespace pfk {
 
-// Whether a system can run on the grouped kernel (stencil operator, PIPEFCG
-// or PIPEGCR, NONE / JACOBI / FP64 INNER_PCG preconditioner); *why says why
-// not.
+// Whether a system can run on the grouped kernel (stencil operator, PIPEFCG,
+// PIPEGCR or PIPEFGMRES, NONE / JACOBI / FP64 INNER_PCG preconditioner); *why
+// says why not.
 bool group_eligible(const pfk_operator* op, const pfk_pc_desc* pc, const pfk_solve_params* prm, const char** why);
 // The method and preconditioner part of that test alone.
 bool group_method_eligible(const pfk_pc_desc* pc, const pfk_solve_params* prm, const char** why);

@@ -462,8 +462,8 @@ def solve_batched(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_it
 
 def solve_grouped(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_iters=4, history: int = 0,
                   ctas_per_system: int = 0, **kw):
-    """Solves independent stencil systems ops[j] x_j = bs[j] with PIPEFCG or
-    PIPEGCR (method=...) on the grouped persistent kernel (a group of CTAs per
+    """Solves independent stencil systems ops[j] x_j = bs[j] with PIPEFCG,
+    PIPEGCR or PIPEFGMRES (method=...) on the grouped persistent kernel (a group of CTAs per
     system, the systems sharing cooperative launches).  bs / x0s are NumPy
     arrays (host path); the preconditioner is FP64.  Returns (xs, infos,
     histories)."""

@@ -1,5 +1,5 @@
-"""Grouped persistent PIPEFCG and PIPEGCR (pfk_solve_grouped, and the
-server's grouped path): each system against the oracle (envelope protocol of tests/_parity.py),
+"""Grouped persistent PIPEFCG, PIPEGCR and PIPEFGMRES (pfk_solve_grouped, and
+the server's grouped path): each system against the oracle (envelope protocol of tests/_parity.py),
 bitwise independence of the batch composition and of the serving order, CTA
 counts from 1 to several per system, the headline regime at 32^3 against the
 stored oracle envelope, and the bounded group barrier's time-out."""
@@ -78,6 +78,41 @@ def test_grouped_pipegcr_first_iterations_strict(ctx):
     assert ref.breakdowns == 0
     assert len(hists[0]) == len(rho) == 13
     assert np.allclose(hists[0][:, 0], rho, rtol=1e-10, atol=0.0)
+
+
+@pytest.mark.parametrize("sigma,ctas", [(1.0, 0), (float("nan"), 3)])
+def test_grouped_pipefgmres_matches_oracle(ctx, sigma, ctas):
+    """PIPEFGMRES (Alg. 15) with constant shift sigma (given, or estimated by
+    the power iteration on both sides) on the grouped kernel, 4 inner FP64
+    Jacobi-PCG iterations, restart length 30, against the oracle."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 25 + j) for j, d in enumerate([(20, 18, 16), (16, 16, 24)])]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, [c["b"] for c in cs], pc_kind="inner_pcg", inner_iters=4,
+                                         history=3000, ctas_per_system=ctas, method="pipefgmres", sigma=sigma,
+                                         mmax=30, rtol=1e-8, maxit=2000, max_restarts=50)
+    for c, info, h in zip(cs, infos, hists):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref, alts = oracle_with_envelope("pipefgmres", aop, lambda: PC.InnerPCG(aop, 4), c["b"],
+                                         K.Params(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50, sigma=sigma))
+        s = check_solve(h, info, ref, alts, rtol=1e-8)
+        assert s["prefix"] >= 5, s
+
+
+def test_grouped_pipefgmres_restart_cycles_strict(ctx):
+    """Restart length 6 with Jacobi (several cycles: least squares, x update,
+    new cycle), 4 CTAs: the history's leading entries against the oracle to
+    1e-10, the whole solve within the envelope."""
+    from paper_1511_07226_gb300 import pfk
+    c = _cube((18, 20, 16), 47)
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    xs, infos, hists = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="jacobi", history=4000, ctas_per_system=4,
+                                         method="pipefgmres", sigma=1.0, mmax=6, rtol=1e-8, maxit=3000)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    prm = K.Params(mmax=6, rtol=1e-8, maxit=3000, sigma=1.0)
+    ref, alts = oracle_with_envelope("pipefgmres", aop, lambda: PC.JacobiPC(aop), c["b"], prm)
+    s = check_solve(hists[0], infos[0], ref, alts, rtol=1e-8)
+    assert s["prefix"] >= 8, s
 
 
 def test_grouped_jacobi_2d_and_3d(ctx):
@@ -185,19 +220,20 @@ def test_grouped_barrier_timeout_is_reported(ctx):
 
 
 def test_server_grouped_requests_bitwise_and_oracle(ctx):
-    """Requests served together through the grouped path (PIPEFCG and PIPEGCR)
-    equal, bit for bit, the same requests solved alone by pfk_solve_grouped; a
-    PIPEFGMRES request in the same stream goes to a whole-GPU worker and equals
-    pfk_solve alone; one served grouped request is also checked against the
-    oracle's envelope."""
+    """Requests served together through the grouped path (PIPEFCG, PIPEGCR,
+    PIPEFGMRES up to group_max_n unknowns) equal, bit for bit, the same
+    requests solved alone by pfk_solve_grouped; a larger request in the same
+    stream goes to a whole-GPU worker and equals pfk_solve alone; one served
+    grouped request is also checked against the oracle's envelope."""
     from paper_1511_07226_gb300 import pfk
     cs = [_cube(d, 90 + j) for j, d in enumerate([(24, 24, 24), (16, 16, 16), (20, 18, 22), (12, 30, 14)])]
-    meths = ["pipefcg", "pipegcr", "pipefcg", "pipegcr"]
-    kw = dict(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50)
-    srv = pfk.Server(ctx, workers=2)
+    meths = ["pipefcg", "pipegcr", "pipefgmres", "pipegcr"]
+    big = _cube((26, 26, 26), 95)
+    kw = dict(mmax=30, rtol=1e-8, maxit=2000, max_restarts=50, sigma=1.0)
+    srv = pfk.Server(ctx, workers=2, group_max_n=16000)
     try:
         tickets = [srv.submit(c["dims"], c["eta"], c["b"], method=m, **kw) for c, m in zip(cs, meths)]
-        tg = srv.submit(cs[1]["dims"], cs[1]["eta"], cs[1]["b"], method="pipefgmres", sigma=1.0, **kw)
+        tg = srv.submit(big["dims"], big["eta"], big["b"], method="pipefgmres", **kw)
         served = [srv.poll(t) for t in tickets]
         xg, ig, _ = srv.poll(tg)
     finally:
@@ -205,12 +241,12 @@ def test_server_grouped_requests_bitwise_and_oracle(ctx):
     for c, m, (x, info, lat) in zip(cs, meths, served):
         op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
         x1, i1, _ = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, method=m, **kw)
-        assert np.array_equal(x, x1[0])
+        assert np.array_equal(x, x1[0]), m
         assert info["iterations"] == i1[0]["iterations"] and info["restarts"] == i1[0]["restarts"]
         assert info["pass_launches"] == i1[0]["pass_launches"] >= 1
-    op = pfk.Operator.stencil(ctx, cs[1]["dims"], cs[1]["eta"])
+    op = pfk.Operator.stencil(ctx, big["dims"], big["eta"])
     pc = pfk.Preconditioner(ctx, op, "inner_pcg", inner_iters=4)
-    x1, i1, _ = pfk.solve(ctx, op, pc, cs[1]["b"], method="pipefgmres", sigma=1.0, **kw)
+    x1, i1, _ = pfk.solve(ctx, op, pc, big["b"], method="pipefgmres", **kw)
     assert np.array_equal(xg, x1) and ig["iterations"] == i1["iterations"]
     # the served solution of the first request against the oracle's
     c = cs[0]

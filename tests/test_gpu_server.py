@@ -1,7 +1,7 @@
 """The continuous-batching server (pfk_server_*): every served result is bit for
 bit the result of the same request solved alone -- through pfk_solve_grouped
-for the small PIPEFCG / PIPEGCR requests the server advances on the grouped
-kernel, through pfk_solve for the rest -- whatever else runs concurrently;
+for the small requests the server advances on the grouped kernel, through
+pfk_solve for the rest -- whatever else runs concurrently;
 admission, queue limit and ticket handling."""
 import time
 
@@ -37,7 +37,7 @@ GROUP_MAX_N = 110592   # the server's default bound of grouped requests
 def _grouped(c, method, group_max_n=0):
     """Whether a default server runs this request on the grouped kernel."""
     bound = GROUP_MAX_N if group_max_n == 0 else group_max_n
-    return method in ("pipefcg", "pipegcr") and c["b"].size <= bound
+    return method in ("pipefcg", "pipegcr", "pipefgmres") and c["b"].size <= bound
 
 
 def _alone(ctx, c, method, group_max_n=0):
@@ -187,7 +187,7 @@ def test_tiny_budget_grouped_requests_one_at_a_time(ctx):
     admitted one at a time in arrival order and each equals its grouped solve
     alone."""
     from paper_1511_07226_gb300 import pfk
-    reqs = [(r, c) for r, c in _requests(12, 14, 26) if METHOD_OF[r["method"]] != "pipefgmres"][:5]
+    reqs = _requests(5, 14, 26)
     srv = pfk.Server(ctx, workers=1, memory_budget=1)
     t0, tickets = [], []
     for r, c in reqs:
@@ -242,7 +242,7 @@ def test_served_results_match_oracle(ctx, method):
     op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
     if _grouped(c, method):
         xs, ias, hs = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=4, method=method,
-                                        history=4000, **KW)
+                                        sigma=1.0, history=4000, **KW)
         xa, ia, hist = xs[0], ias[0], hs[0]
     else:
         pc = pfk.Preconditioner(ctx, op, "inner_pcg", 4, "fp64")
