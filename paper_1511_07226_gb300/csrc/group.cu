@@ -15,16 +15,19 @@
 // <r_i, w_i>, delta_i = <w_i, w_i>, ||r_i||^2 and <w_i, s_k>.  PIPEFGMRES
 // (Alg. 15) forms p_k, u_k, zbar_k and the dots of Hessenberg column k in one
 // pass; every CTA keeps the Givens rotations, and a restart cycle ends with
-// the least-squares solution and x = x_0 + U y.  A reduction writes one partial row per CTA; the CTAs meet at the
-// system's own barrier (an arrival counter and a generation word of that
-// system, with bounded waits) and every CTA sums the rows in rank order, so
-// all CTAs of the group hold bitwise the same scalars and run the scalar
-// phase themselves.  An operator application that reads other CTAs' rows
+// the least-squares solution and x = x_0 + U y.
+//
+// A reduction writes one partial row per CTA; the CTAs meet at the system's
+// own barrier (an arrival counter and a generation word of that system, with
+// bounded waits) and every CTA sums the rows in rank order, so all CTAs of
+// the group hold bitwise the same scalars and run the scalar phase
+// themselves.  An operator application that reads other CTAs' rows
 // (the stencil's neighbouring planes) first waits at the system's barrier for
 // its input vector to be complete.  Nothing waits for another system.
 //
 // The solve is resumable: a launch advances each system by at most `iters`
-// steps (a step is an iteration or a pipeline fill) and leaves its scalars in
+// steps (a step is an iteration, a pipeline fill or a PIPEFGMRES cycle start
+// with its first column) and leaves its scalars in
 // the system's state record, so the host can retire finished systems and
 // admit new ones between launches (continuous batching).  Restarts on norm
 // breakdown and residual replacement (the true-residual check at
@@ -54,7 +57,7 @@ constexpr int kGrpMaxInner = 64;             // inner PCG iterations
 enum GrpPhase { kGStart = 0, kGFill = 1, kGIter = 2, kGDone = 3 };
 
 struct GrpParams {
-  int method;                 // PFK_PIPEFCG or PFK_PIPEGCR
+  int method;                 // PFK_PIPEFCG, PFK_PIPEGCR or PFK_PIPEFGMRES
   int mmax, truncation, norm, maxit, max_restarts, true_check;
   double rtol, atol;
   int pc_kind, pc_inner;
@@ -102,9 +105,10 @@ struct GrpSys {
   const double* b;
   double* x;
   double* ws;         // r, u, w, m, n, t, tmp, then rings P, S, Q, Z of mmax + 1 slots
+                      // (PIPEFGMRES: r, qbar, wbar at 0, n, 2n; then p_j, u_j, zbar_j at 7n)
   double* pcws;       // inner PCG: r, p, s, x
   double* part;       // [2][nblk][kGrpNd] partial rows
-  double* gm;         // PIPEFGMRES: rotated Hessenberg R [(m+1) x m], then y [m]
+  double* gm;         // PIPEFGMRES: rotated Hessenberg columns R [(m+1) x m] (rank 0 writes)
   double* hist;
   int hist_cap, pad;
   GrpParams P;
@@ -1349,7 +1353,7 @@ bool GroupRunner::any_active() const { return m_->used_ctas > 0; }
 int64_t GroupRunner::workspace_bytes(int64_t n, int mmax, int nblk) {
   const int64_t slots = mmax + 1;
   return (int64_t)sizeof(double) *
-             ((7 + 4 * slots) * n + 4 * n + 2 * (int64_t)nblk * kGrpNd + (int64_t)(mmax + 2) * mmax) +
+             ((7 + 4 * slots) * n + 4 * n + 2 * (int64_t)nblk * kGrpNd + (int64_t)(mmax + 1) * mmax) +
          256;
 }
 
