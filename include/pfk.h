@@ -391,10 +391,14 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
  *    nsys consecutive blocks of history_capacity entries.
  *  - b[j], x[j]: host (ptrs_on_device = 0) or device (1) vectors of length
  *    n_j; x[j] holds x0 on entry and the solution on exit.
- *  - ctas_per_system: 1..64, or 0 for about one CTA per 4,096 cells (at most
- *    64, at most one per x-row).  infos[j].pass_launches reports the CTA
- *    count used, time_ms the device time of all launches, kernel_launches
- *    their number.
+ *  - ctas_per_system: 1..64; 0 for about one CTA per 4,096 cells; -1 for a
+ *    size chosen by timing: on the first call for a (device, size bucket =
+ *    ceil log2 of the largest n, method, preconditioner) key, the systems
+ *    that fit one launch run their fill and two timed steps at 2,048, 4,096,
+ *    8,192 and 16,384 cells per CTA (x restored afterwards) and the fastest
+ *    per cell is kept for the process.  Always at most 64 and at most one
+ *    per x-row.  infos[j].pass_launches reports the CTA count used, time_ms
+ *    the device time of all launches, kernel_launches their number.
  * Returns PFK_OK if every system converged, else the first non-OK status of
  * a system; PFK_ERR_INVALID for an ineligible system or a system needing more
  * CTAs than the GPU holds at once. */

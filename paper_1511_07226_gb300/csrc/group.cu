@@ -42,7 +42,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 namespace pfk {
@@ -1269,14 +1272,25 @@ bool group_eligible(const pfk_operator* op, const pfk_pc_desc* pcd, const pfk_so
   return group_method_eligible(pcd, prm, why);
 }
 
-// CTAs of a system: about kGrpCellsPerCta cells each, at most kGrpMaxCtas and
-// at most one per x-row (a group's CTAs own whole rows).
-int group_ctas(int64_t n, int64_t rows, int requested) {
-  int64_t c = requested > 0 ? requested : (n + kGrpCellsPerCta - 1) / kGrpCellsPerCta;
+// CTAs of a system at about `cells` cells each, at most kGrpMaxCtas and at
+// most one per x-row (a group's CTAs own whole rows).
+static int group_ctas_cells(int64_t n, int64_t rows, int64_t cells) {
+  int64_t c = (n + cells - 1) / cells;
   c = std::min<int64_t>(c, kGrpMaxCtas);
   c = std::min<int64_t>(c, rows);
   return (int)std::max<int64_t>(c, 1);
 }
+
+int group_ctas(int64_t n, int64_t rows, int requested) {
+  if (requested > 0) return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)requested, kGrpMaxCtas, rows}));
+  return group_ctas_cells(n, rows, kGrpCellsPerCta);
+}
+
+// Cells per CTA chosen by timing (ctas_per_system = -1), per device, size
+// bucket (ceil log2 of the batch's largest system), method and
+// preconditioner; kept for the process.
+static std::mutex g_tuned_mu;
+static std::map<std::tuple<int, int, int, int, int>, int64_t> g_tuned_cells;
 
 struct GroupRunner::Impl {
   pfk_context* ctx = nullptr;
@@ -1513,8 +1527,8 @@ extern "C" pfk_status pfk_solve_grouped(pfk_context* ctx, int nsys, const pfk_op
     set_error(ctx, "invalid argument");
     return PFK_ERR_INVALID;
   }
-  if (ctas_per_system < 0 || ctas_per_system > kGrpMaxCtas) {
-    set_error(ctx, "ctas_per_system must be 0 (automatic) or 1..64");
+  if (ctas_per_system < -1 || ctas_per_system > kGrpMaxCtas) {
+    set_error(ctx, "ctas_per_system must be -1 (tuned), 0 (automatic) or 1..64");
     return PFK_ERR_INVALID;
   }
   for (int j = 0; j < nsys; ++j) {
@@ -1530,8 +1544,9 @@ extern "C" pfk_status pfk_solve_grouped(pfk_context* ctx, int nsys, const pfk_op
   pfk_status ps = R.init(ctx, 0);
   if (ps != PFK_OK) return ps;
   std::vector<int> nblk(nsys);
+  auto rows_of = [&](int j) { return (int64_t)ops[j]->ny * ops[j]->nz; };
   for (int j = 0; j < nsys; ++j) {
-    nblk[j] = group_ctas(ops[j]->n, (int64_t)ops[j]->ny * ops[j]->nz, ctas_per_system);
+    nblk[j] = group_ctas(ops[j]->n, rows_of(j), ctas_per_system > 0 ? ctas_per_system : 0);
     if (nblk[j] > R.capacity_ctas()) {
       set_error(ctx, "a system needs more CTAs than the GPU holds at once");
       return PFK_ERR_INVALID;
@@ -1570,6 +1585,72 @@ extern "C" pfk_status pfk_solve_grouped(pfk_context* ctx, int nsys, const pfk_op
     }
   }
   if (hcap) PFK_CUDA(ctx, cudaMemsetAsync(dhist, 0xff, sizeof(double) * (size_t)nsys * hcap * PFK_HISTORY_FIELDS, st));
+  if (ctas_per_system == -1) {
+    // tuned group size: per candidate, the systems that fit one launch run
+    // their start and fill, then two timed steps; x is restored afterwards
+    int64_t nmax = 0;
+    for (int j = 0; j < nsys; ++j) nmax = std::max(nmax, ops[j]->n);
+    const auto key = std::make_tuple(ctx->device, (int)std::ceil(std::log2((double)std::max<int64_t>(nmax, 2))),
+                                     (int)prm->method, pcd ? (int)pcd->kind : 0, pcd ? (int)pcd->inner_iters : 0);
+    int64_t cells = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_tuned_mu);
+      auto f = g_tuned_cells.find(key);
+      if (f != g_tuned_cells.end()) cells = f->second;
+    }
+    if (cells == 0) {
+      double* xsave = nullptr;
+      PFK_CUDA(ctx, cudaMallocAsync((void**)&xsave, sizeof(double) * (size_t)ntot, st));
+      struct FreeX {
+        double* p; cudaStream_t s;
+        ~FreeX() { if (p) cudaFreeAsync(p, s); }
+      } xguard{xsave, st};
+      {
+        int64_t off = 0;
+        for (int j = 0; j < nsys; ++j) {
+          PFK_CUDA(ctx, cudaMemcpyAsync(xsave + off, xd[j], ops[j]->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          off += ops[j]->n;
+        }
+      }
+      double best = -1.0;
+      for (int64_t cand : {2048, 4096, 8192, 16384}) {
+        GroupRunner T;
+        ps = T.init(ctx, 0);
+        if (ps != PFK_OK) return ps;
+        std::vector<int> slots;
+        double work = 0.0;
+        for (int j = 0; j < nsys; ++j) {
+          const int c = group_ctas_cells(ops[j]->n, rows_of(j), cand);
+          if (c > T.free_ctas()) break;
+          int sl = -1;
+          ps = T.admit(ops[j], pcd, prm, bd[j], xd[j], c, nullptr, 0, &sl);
+          if (ps != PFK_OK) return ps;
+          slots.push_back(sl);
+          work += (double)ops[j]->n;
+        }
+        if (slots.empty()) continue;
+        if ((ps = T.step(1)) != PFK_OK) return ps;
+        const double t0 = T.kernel_ms();
+        if ((ps = T.step(2)) != PFK_OK) return ps;
+        const double rate = work / std::max(T.kernel_ms() - t0, 1e-6);
+        if (rate > best) {
+          best = rate;
+          cells = cand;
+        }
+        for (int sl : slots) T.release(sl);
+        int64_t off = 0;
+        for (int j = 0; j < nsys; ++j) {
+          PFK_CUDA(ctx, cudaMemcpyAsync(xd[j], xsave + off, ops[j]->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          off += ops[j]->n;
+        }
+      }
+      PFK_CUDA(ctx, cudaStreamSynchronize(st));
+      if (cells == 0) cells = kGrpCellsPerCta;
+      std::lock_guard<std::mutex> lk(g_tuned_mu);
+      g_tuned_cells[key] = cells;
+    }
+    for (int j = 0; j < nsys; ++j) nblk[j] = group_ctas_cells(ops[j]->n, rows_of(j), cells);
+  }
   // admission in the given order; iterations chunked so that finished
   // systems make room for the next ones
   std::vector<int> slot_of(nsys, -1), state(nsys, 0);   // 0 queued, 1 active, 2 done

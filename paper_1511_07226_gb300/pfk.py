@@ -463,10 +463,11 @@ def solve_batched(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_it
 def solve_grouped(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_iters=4, history: int = 0,
                   ctas_per_system: int = 0, **kw):
     """Solves independent stencil systems ops[j] x_j = bs[j] with PIPEFCG,
-    PIPEGCR or PIPEFGMRES (method=...) on the grouped persistent kernel (a group of CTAs per
-    system, the systems sharing cooperative launches).  bs / x0s are NumPy
-    arrays (host path); the preconditioner is FP64.  Returns (xs, infos,
-    histories)."""
+    PIPEGCR or PIPEFGMRES (method=...) on the grouped persistent kernel (a
+    group of CTAs per system, the systems sharing cooperative launches;
+    ctas_per_system 1..64, 0 = about one per 4,096 cells, -1 = chosen by
+    timing and cached).  bs / x0s are NumPy arrays (host path); the
+    preconditioner is FP64.  Returns (xs, infos, histories)."""
     lib = load()
     nsys = len(ops)
     prm = make_params(**kw)

@@ -163,6 +163,28 @@ def test_grouped_composition_and_cta_count(ctx):
     assert np.allclose(h2[0][:k, 0], hists[0][:k, 0], rtol=1e-11, atol=0.0)
 
 
+def test_grouped_tuned_group_size(ctx):
+    """ctas_per_system = -1: the group size is chosen by timing trials (x
+    restored afterwards) and cached; the solve then equals, bit for bit, the
+    same batch with that CTA count given explicitly, and a second tuned call
+    reuses the cached choice."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube((28, 28, 28), 100 + j) for j in range(6)]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    bs = [c["b"] for c in cs]
+    kw = dict(pc_kind="inner_pcg", inner_iters=4, history=3000, mmax=30, rtol=1e-8, maxit=2000)
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, bs, ctas_per_system=-1, **kw)
+    ctas = infos[0]["pass_launches"]
+    assert all(i["pass_launches"] == ctas for i in infos)
+    assert ctas in {-(-28 ** 3 // c) for c in (2048, 4096, 8192, 16384)}
+    x2, i2, h2 = pfk.solve_grouped(ctx, ops, bs, ctas_per_system=ctas, **kw)
+    x3, i3, h3 = pfk.solve_grouped(ctx, ops, bs, ctas_per_system=-1, **kw)
+    for j in range(len(cs)):
+        assert np.array_equal(xs[j], x2[j]) and np.array_equal(xs[j], x3[j])
+        assert np.array_equal(hists[j], h2[j], equal_nan=True)
+        assert infos[j]["status_name"] == "ok"
+
+
 def test_grouped_nonzero_initial_guess_and_restart_truncation(ctx):
     from paper_1511_07226_gb300 import pfk
     cs = [_cube(d, 60 + j) for j, d in enumerate([(18, 18, 18), (26, 14, 12)])]
