@@ -22,7 +22,11 @@ Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: dense LU, Krylov-subspace minimisation by brute force, closed-form
 Chebyshev error polynomials, finite termination, orthogonality invariants and
 the toy experiment of Fig. FCGtoy.  The mixed-precision (FP32 / BF16
-coefficient) preconditioner emulations are "parity unpinned": the paper fixes
-no reduced-precision arithmetic.
+coefficient) preconditioner emulations follow a stated rounding model (the
+paper fixes no reduced-precision arithmetic) and are pinned by its
+properties: representability and unit-roundoff bounds of the coefficient
+copies, the error bound of the reduced-precision operator, the closed-form
+Chebyshev error polynomial with the rounded D^-1, and the one-cell inner
+PCG.
 """
 from . import operators, preconditioners, krylov  # noqa: F401

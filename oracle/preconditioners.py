@@ -26,8 +26,11 @@ mixed-precision preconditioners: the preconditioner's copy of A stores the
 diagonal, the interior face coefficients and D^-1, each rounded
 FP64 -> FP32 (-> BF16, round to nearest even); constant advection weights stay
 FP32; vector arithmetic is FP32; inner products are accumulated in FP64 from
-the FP32 values.  The paper fixes no reduced-precision arithmetic, so these
-are "parity unpinned" (checked by tolerance only).
+the FP32 values.  The paper fixes no reduced-precision arithmetic; this
+rounding model is the reading, pinned by its properties (format
+representability and unit-roundoff bounds of the copies, the copy's operator
+error bound, the Chebyshev closed form with the rounded D^-1, the one-cell
+inner PCG).
 """
 from __future__ import annotations
 

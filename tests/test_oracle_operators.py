@@ -207,9 +207,99 @@ def test_jacobi_and_noisy_pc():
     assert np.allclose((out - v) / np.linalg.norm(out - v), bank[0] / np.linalg.norm(bank[0]))
 
 
+_UNIT = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -8}   # unit roundoff of the coefficient format
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_rounded_stencil_coefficients_and_error_bound(precision):
+    """The preconditioner's reduced-precision operator copy: every stored
+    coefficient is a number of the target format (rounding is idempotent)
+    within its unit roundoff of the FP64 value; y = A~ u on an FP32 vector is
+    within the bound of a 7-term FP32 sum plus the coefficient rounding of the
+    FP64 product sum |a_ij| |u_j|, and (BF16) far enough from it that the
+    coefficient rounding shows."""
+    c = W.poisson3d_gaussian(dims=(7, 6, 5), log_contrast=2.0, config_id=900, item_id=31)
+    op = O.StencilOperator(c["dims"], c["eta"], (1.5, -0.5, 0.8))
+    rs = PC.RoundedStencil(op, precision)
+    u = _UNIT[precision]
+    d64 = op.diagonal().reshape(op.shape)
+    for got, ref in [(rs.d, d64), (rs.dinv, 1.0 / d64)]:
+        assert got.dtype == np.float32
+        if precision == "bf16":
+            assert np.array_equal(PC.bf16_round(got), got)
+        assert np.all(np.abs(got.astype(np.float64) - ref) <= u * np.abs(ref))
+    a = op.to_dense()
+    x = W.random_vector(op.n, 32).astype(np.float32)
+    y = rs.apply(x).astype(np.float64)
+    scale = np.abs(a) @ np.abs(x.astype(np.float64))
+    rel = np.abs(y - a @ x.astype(np.float64)) / scale
+    assert rel.max() <= u + 8 * 2.0 ** -24, rel.max()
+    if precision == "bf16":
+        assert rel.max() >= 0.1 * u
+
+
+def _cheb_closed_form(a, dinv, v, k, lo, hi):
+    """x_k = (I - P_k(M)) A^-1 v, M = diag(dinv) A, from the eigenvectors of the
+    symmetric diag(dinv)^1/2 A diag(dinv)^1/2."""
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    gh = np.sqrt(dinv)
+    mu, q = np.linalg.eigh(gh[:, None] * a * gh[None, :])
+    ck = np.zeros(k + 1)
+    ck[k] = 1.0
+    pk = np.polynomial.chebyshev.chebval((theta - mu) / delta, ck) / \
+        np.polynomial.chebyshev.chebval(theta / delta, ck)
+    xstar = np.linalg.solve(a, v)
+    return xstar - (gh[:, None] * q) @ (pk * (q.T @ (xstar / gh))), xstar
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_reduced_precision_chebyshev_closed_form(precision, k):
+    """Constant eta (every face and diagonal coefficient an integer, exact in
+    both formats): the reduced-precision Chebyshev sweeps give the closed-form
+    error polynomial of M = D~^-1 A with D~^-1 the diagonal's inverse rounded to
+    the format, to FP32 accuracy -- and (BF16) not that of the exact D^-1."""
+    op = O.StencilOperator((6, 5, 4), np.ones(120))
+    a = op.to_dense()
+    d = np.diag(a)
+    assert np.array_equal(d, np.round(d))
+    dinv = (1.0 / d).astype(np.float32)
+    if precision == "bf16":
+        dinv = PC.bf16_round(dinv)
+    v = W.random_vector(120, 21)
+    lo, hi = 0.05, 2.0
+    x = PC.Chebyshev(op, k, lo=lo, hi=hi, precision=precision)(v)
+    assert np.array_equal(x, x.astype(np.float32).astype(np.float64))
+    exp, xstar = _cheb_closed_form(a, dinv.astype(np.float64), v, k, lo, hi)
+    assert np.linalg.norm(x - exp) <= 1e-6 * np.linalg.norm(xstar)
+    if precision == "bf16":
+        exact, _ = _cheb_closed_form(a, 1.0 / d, v, k, lo, hi)
+        assert np.linalg.norm(x - exact) >= 1e-4 * np.linalg.norm(xstar)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("k", [1, 3])
+def test_reduced_precision_inner_pcg_one_cell(precision, k):
+    """One cell: Jacobi-PCG converges in one step to v / d~, d~ the diagonal as
+    the preconditioner's copy stores it (the format's rounding of d), to FP32
+    accuracy; the result is an FP32 number."""
+    op = O.StencilOperator((1, 1, 1), np.array([2.7]))
+    d = op.diagonal()[0]
+    dr = np.float32(d)
+    if precision == "bf16":
+        dr = PC.bf16_round(np.array([dr]))[0]
+    v = np.array([0.37])
+    x = PC.InnerPCG(op, k, precision=precision)(v)
+    assert x[0] == np.float64(np.float32(x[0]))
+    assert abs(x[0] - 0.37 / float(dr)) <= 4 * 2.0 ** -24 * abs(x[0])
+    if precision == "bf16":
+        assert abs(x[0] - 0.37 / d) >= 1e-4 * abs(x[0])
+
+
 @pytest.mark.parametrize("precision,tol", [("fp32", 3e-6), ("bf16", 2e-2)])
 def test_reduced_precision_preconditioners_close_to_fp64(precision, tol):
-    """Parity unpinned (no paper definition): only closeness to the FP64 form is checked."""
+    """On a variable-coefficient problem with advection the reduced-precision
+    forms stay close to the FP64 ones (the pins above fix their rounding)."""
     c = W.poisson3d_gaussian(dims=(12, 10, 8), log_contrast=1.0, config_id=900, item_id=13)
     op = O.StencilOperator(c["dims"], c["eta"], (2.0, 1.0, -1.0))
     v = W.random_vector(op.n, 14)
