@@ -73,8 +73,8 @@ def test_batched_3d_and_jacobi(ctx):
 
 
 def test_batched_fp32_preconditioner(ctx):
-    """Mixed precision (parity unpinned): FP32 inner CG under FP64 recurrences must
-    still meet the FP64 true-residual tolerance."""
+    """Mixed precision: FP32 inner CG under FP64 recurrences must still meet the
+    FP64 true-residual tolerance."""
     from paper_1511_07226_gb300 import pfk
     sys = _systems([48, 96, 32])
     ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in sys]
