@@ -658,6 +658,16 @@ def extra_batched(ctx, dev, args) -> dict:
     kern_ms = max(i["time_ms"] for i in infos)
     unknowns = int(sum(int(s) ** 2 for s in sides))
     conv = int(sum(i["status_name"] == "ok" for i in infos))
+    # the same batch on the grouped kernel (a CTA group per system, size tuned)
+    pfk.solve_grouped(ctx, ops, bs, ctas_per_system=-1, **kw)
+    ginfos = pfk.solve_grouped(ctx, ops, bs, ctas_per_system=-1, **kw)[1]
+    gkern = ginfos[0]["time_ms"]
+    gconv = int(sum(i["status_name"] == "ok" for i in ginfos))
+    grouped = {"kernel_ms": gkern, "converged": gconv, "solves_per_s": gconv / (gkern / 1e3),
+               "system_iterations_per_s": float(sum(i["iterations"] for i in ginfos)) / (gkern / 1e3),
+               "ctas_per_system_max": int(max(i["pass_launches"] for i in ginfos)),
+               "launches": int(ginfos[0]["kernel_launches"]),
+               "max_true_rel_residual": float(max(i["rnorm_true"] / i["bnorm"] for i in ginfos))}
     # the same batch with restart-style truncation (Sec. 5 remark): the
     # truncation the 128^3 sweep shows curing most of the stagnation
     rinfos = pfk.solve_batched(ctx, ops, bs, **dict(kw, truncation="restart"))[1]
@@ -692,7 +702,7 @@ def extra_batched(ctx, dev, args) -> dict:
             "roofline": {"bound": "hbm", "achieved_gbs": achieved, "peak_gbs": hbm, "frac": achieved / hbm,
                          "alg_bytes_per_unknown_iteration": bytes_it, "mean_unknowns": mean_n,
                          "note": "algorithmic bytes of all system-iterations over the launch time"},
-            "restart_truncation": restart_trunc}
+            "restart_truncation": restart_trunc, "grouped_kernel": grouped}
 
 
 def extra_config1(ctx, dev, args) -> dict:

@@ -385,7 +385,9 @@ pfk_status pfk_solve_batched(pfk_context* ctx, int nsys, const pfk_operator* con
  * iterations, breakdown restarts and the true-residual check run as in
  * pfk_solve.
  *  - ops[j]: matrix-free stencil operators; pc: NONE, JACOBI or INNER_PCG in
- *    FP64 (1..64 inner iterations), the same description for all systems.
+ *    FP64 or FP32 (1..64 inner iterations; FP32: vectors and coefficient
+ *    copies in FP32, inner products accumulated in FP64), the same
+ *    description for all systems.
  *  - params: method PFK_PIPEFCG, PFK_PIPEGCR or PFK_PIPEFGMRES; graph_iters, profile and persistent are
  *    ignored; barrier_timeout_us as for pfk_solve; history (if set) holds
  *    nsys consecutive blocks of history_capacity entries.
@@ -442,7 +444,7 @@ typedef struct {
   int32_t order;           /* pfk_serve_order; 0 = FIFO */
   int32_t group_max_n;     /* requests of at most this many unknowns that the grouped
                               kernel can run (pfk_solve_grouped: stencil, PIPEFCG,
-                              PIPEGCR or PIPEFGMRES, NONE / JACOBI / FP64 INNER_PCG) are
+                              PIPEGCR or PIPEFGMRES, NONE / JACOBI / INNER_PCG) are
                               advanced together on
                               it; 0 = 110,592 (48^3), < 0 = never */
   int32_t group_ctas;      /* CTAs per grouped request, as pfk_solve_grouped's

@@ -9,8 +9,8 @@
 // group alone: the pipeline fill, the fused pass (the deferred MAXPYs of the
 // previous iteration, the advance of x, r, u, w, the dots gamma_i, delta_i,
 // ||r_i||^2 and the window dots <u_i, s_k>), the preconditioner (none,
-// Jacobi, or k inner Jacobi-PCG iterations, Alg. 3, in FP64) and the
-// operator.  PIPEGCR (Alg. 11) splits the pass in two: the deferred MAXPYs
+// Jacobi, or k inner Jacobi-PCG iterations, Alg. 3, in FP64 or FP32) and
+// the operator.  PIPEGCR (Alg. 11) splits the pass in two: the deferred MAXPYs
 // with the advance of x, r, u, then w_i = A u_i with the dots gamma_i =
 // <r_i, w_i>, delta_i = <w_i, w_i>, ||r_i||^2 and <w_i, s_k>.  PIPEFGMRES
 // (Alg. 15) forms p_k, u_k, zbar_k and the dots of Hessenberg column k in one
@@ -50,6 +50,8 @@
 
 namespace pfk {
 
+pfk_status ensure_reduced_copies(pfk_operator* op, int precision);
+
 constexpr int kGrpThreads = 256;
 constexpr int kGrpNW = PFK_MAX_MMAX;         // window buffer of the pass (columns)
 constexpr int kGrpNd = PFK_MAX_MMAX + 4;     // longest partial row
@@ -64,6 +66,7 @@ struct GrpParams {
   int mmax, truncation, norm, maxit, max_restarts, true_check;
   double rtol, atol;
   int pc_kind, pc_inner;
+  int pc_fp32, pad_p;         // inner PCG in FP32 (vectors and coefficient copies)
   long long bar_timeout_ns;   // bound of each barrier wait (<= 0: no wait allowed)
   double sigma;               // PIPEFGMRES shift; NaN: estimated at the start
 };
@@ -100,6 +103,11 @@ struct GrpSys {
   const double* ky;
   const double* kz;
   const double* dinv;
+  const float* d32;   // FP32 coefficient copies (FP32 inner PCG)
+  const float* kx32;
+  const float* ky32;
+  const float* kz32;
+  const float* dinv32;
   double a0, a1, a2;
   int u0, u1, u2;
   int adv;            // any advection weight non-zero
@@ -244,35 +252,57 @@ __device__ void grp_sum(const GrpSys& S, GrpCta* g, const double (&v)[ND], doubl
          i += 32)                                                                                    \
       for (int64_t c = row_ * (S).nx + i, once_ = 1; once_; once_ = 0)
 
+// The operator's coefficients in the arithmetic type V of a kernel phase: the
+// FP64 arrays, or the FP32 copies of the FP32 inner preconditioner.
+template <typename V>
+struct GrpCoef {
+  const V* d;
+  const V* kx;
+  const V* ky;
+  const V* kz;
+  const V* dinv;
+};
+
 // (A m)_c for cell c = (i, j, k): diffusion faces and upwind advection, fused
-// multiply-adds in a fixed order.  m is written by other CTAs during the
+// multiply-adds in a fixed order, in V.  m is written by other CTAs during the
 // launch, so its loads go to L2 (never a stale L1 line).
-__device__ __forceinline__ double grp_row(const GrpSys& S, const double* m, int64_t c, int i, int j, int k) {
+template <typename V>
+__device__ __forceinline__ V grp_row_t(const GrpSys& S, const GrpCoef<V>& A, const V* m, int64_t c, int i, int j,
+                                       int k) {
   const int64_t sxy = (int64_t)S.nx * S.ny;
   if (!S.adv) {
     // pure diffusion: the same products without the zero advection weights
-    // (adding +0.0 to a coefficient changes nothing)
-    double acc = S.d[c] * __ldcg(m + c);
-    if (i > 0) acc = fma(-S.kx[c - 1], __ldcg(m + c - 1), acc);
-    if (i < S.nx - 1) acc = fma(-S.kx[c], __ldcg(m + c + 1), acc);
-    if (j > 0) acc = fma(-S.ky[c - S.nx], __ldcg(m + c - S.nx), acc);
-    if (j < S.ny - 1) acc = fma(-S.ky[c], __ldcg(m + c + S.nx), acc);
+    // (adding +0 to a coefficient changes nothing)
+    V acc = A.d[c] * __ldcg(m + c);
+    if (i > 0) acc = fma(-A.kx[c - 1], __ldcg(m + c - 1), acc);
+    if (i < S.nx - 1) acc = fma(-A.kx[c], __ldcg(m + c + 1), acc);
+    if (j > 0) acc = fma(-A.ky[c - S.nx], __ldcg(m + c - S.nx), acc);
+    if (j < S.ny - 1) acc = fma(-A.ky[c], __ldcg(m + c + S.nx), acc);
     if (S.ndim == 3) {
-      if (k > 0) acc = fma(-S.kz[c - sxy], __ldcg(m + c - sxy), acc);
-      if (k < S.nz - 1) acc = fma(-S.kz[c], __ldcg(m + c + sxy), acc);
+      if (k > 0) acc = fma(-A.kz[c - sxy], __ldcg(m + c - sxy), acc);
+      if (k < S.nz - 1) acc = fma(-A.kz[c], __ldcg(m + c + sxy), acc);
     }
     return acc;
   }
-  double acc = S.d[c] * __ldcg(m + c);
-  if (i > 0) acc = fma(-(S.kx[c - 1] + (S.u0 == -1 ? S.a0 : 0.0)), __ldcg(m + c - 1), acc);
-  if (i < S.nx - 1) acc = fma(-(S.kx[c] + (S.u0 == 1 ? S.a0 : 0.0)), __ldcg(m + c + 1), acc);
-  if (j > 0) acc = fma(-(S.ky[c - S.nx] + (S.u1 == -1 ? S.a1 : 0.0)), __ldcg(m + c - S.nx), acc);
-  if (j < S.ny - 1) acc = fma(-(S.ky[c] + (S.u1 == 1 ? S.a1 : 0.0)), __ldcg(m + c + S.nx), acc);
+  const V a0 = (V)S.a0, a1 = (V)S.a1, a2 = (V)S.a2;
+  V acc = A.d[c] * __ldcg(m + c);
+  if (i > 0) acc = fma(-(A.kx[c - 1] + (S.u0 == -1 ? a0 : V(0))), __ldcg(m + c - 1), acc);
+  if (i < S.nx - 1) acc = fma(-(A.kx[c] + (S.u0 == 1 ? a0 : V(0))), __ldcg(m + c + 1), acc);
+  if (j > 0) acc = fma(-(A.ky[c - S.nx] + (S.u1 == -1 ? a1 : V(0))), __ldcg(m + c - S.nx), acc);
+  if (j < S.ny - 1) acc = fma(-(A.ky[c] + (S.u1 == 1 ? a1 : V(0))), __ldcg(m + c + S.nx), acc);
   if (S.ndim == 3) {
-    if (k > 0) acc = fma(-(S.kz[c - sxy] + (S.u2 == -1 ? S.a2 : 0.0)), __ldcg(m + c - sxy), acc);
-    if (k < S.nz - 1) acc = fma(-(S.kz[c] + (S.u2 == 1 ? S.a2 : 0.0)), __ldcg(m + c + sxy), acc);
+    if (k > 0) acc = fma(-(A.kz[c - sxy] + (S.u2 == -1 ? a2 : V(0))), __ldcg(m + c - sxy), acc);
+    if (k < S.nz - 1) acc = fma(-(A.kz[c] + (S.u2 == 1 ? a2 : V(0))), __ldcg(m + c + sxy), acc);
   }
   return acc;
+}
+
+__device__ __forceinline__ GrpCoef<double> grp_coef64(const GrpSys& S) {
+  return GrpCoef<double>{S.d, S.kx, S.ky, S.kz, S.dinv};
+}
+
+__device__ __forceinline__ double grp_row(const GrpSys& S, const double* m, int64_t c, int i, int j, int k) {
+  return grp_row_t<double>(S, grp_coef64(S), m, c, i, j, k);
 }
 
 // y = A m, or y = bsub - A m, on the CTA's cells.  m must be complete on
@@ -285,6 +315,126 @@ __device__ void grp_apply(const GrpSys& S, GrpCta* g, const double* m, double* y
     y[c] = bsub ? bsub[c] - v : v;
   }
   __syncthreads();
+}
+
+// Inner Jacobi-PCG in V (FP64, or FP32 vectors and coefficient copies with
+// the inner products of FP32 values accumulated in FP64): out = add + x_k.
+template <typename V>
+__device__ void grp_pcg(const GrpSys& S, GrpCta* g, const GrpCoef<V>& A, const double* v, double* out,
+                        const double* add, double* s_red) {
+  const int64_t n = S.n;
+  V* r = (V*)S.pcws;
+  V* p = r + n;
+  V* s = p + n;
+  V* x = s + n;
+  const V* dinv = A.dinv;
+  const int kk = S.P.pc_inner;
+  {
+    // r_0 = v; gamma_0 = <D^-1 r_0, r_0>
+    double acc[1] = {0.0};
+    #pragma unroll 4
+    GRP_ELEMS(S, g, e) {
+      const V rv = (V)v[e];
+      r[e] = rv;
+      const V z = dinv[e] * rv;
+      acc[0] += (double)z * (double)rv;
+    }
+    grp_sum<1>(S, g, acc, s_red);
+    if (threadIdx.x == 0) {
+      g->pg = g->red[0];
+      g->last_x = g->pg == 0.0 ? 0 : kk;
+    }
+    __syncthreads();
+  }
+  if (g->last_x > 0) {
+    // p_0 = D^-1 r_0, s_0 = A p_0, eta_0 = <s_0, p_0>
+    #pragma unroll 4
+    GRP_ELEMS(S, g, e) p[e] = dinv[e] * r[e];
+    grp_barrier(S, g);
+    double acc[1] = {0.0};
+    #pragma unroll 2
+    GRP_ROWS(S, g, c, i, j, k) {
+      const V sv = grp_row_t<V>(S, A, p, c, i, j, k);
+      s[c] = sv;
+      acc[0] += (double)sv * (double)p[c];
+    }
+    grp_sum<1>(S, g, acc, s_red);
+    if (threadIdx.x == 0) {
+      if (g->red[0] == 0.0) g->last_x = 0;
+      else g->palpha[0] = g->pg / g->red[0];
+    }
+    __syncthreads();
+  }
+  for (int it = 1; it < kk; ++it) {
+    if (it > g->last_x) break;
+    {
+      // r_i = r_{i-1} - alpha_{i-1} s_{i-1}; gamma_i
+      const V al = (V)g->palpha[it - 1];
+      double acc[1] = {0.0};
+      #pragma unroll 4
+      GRP_ELEMS(S, g, e) {
+        const V rv = r[e] - al * s[e];
+        r[e] = rv;
+        const V z = dinv[e] * rv;
+        acc[0] += (double)z * (double)rv;
+      }
+      grp_sum<1>(S, g, acc, s_red);
+      if (threadIdx.x == 0) {
+        const double gn = g->red[0];
+        if (gn == 0.0) {
+          g->last_x = it;
+        } else {
+          g->pbeta = gn / g->pg;
+          g->pg = gn;
+        }
+      }
+      __syncthreads();
+    }
+    {
+      // x_i = x_{i-1} + alpha_{i-1} p_{i-1}; p_i = D^-1 r_i + beta_i p_{i-1}
+      const V al = (V)g->palpha[it - 1];
+      const V be = (V)g->pbeta;
+      const bool do_p = it < g->last_x;
+      #pragma unroll 4
+      GRP_ELEMS(S, g, e) {
+        const V po = p[e];
+        x[e] = (it == 1 ? V(0) : x[e]) + al * po;
+        if (do_p) p[e] = dinv[e] * r[e] + be * po;
+      }
+      if (!do_p) {
+        __syncthreads();
+        break;
+      }
+      grp_barrier(S, g);
+    }
+    {
+      // s_i = A p_i, eta_i
+      double acc[1] = {0.0};
+      #pragma unroll 2
+      GRP_ROWS(S, g, c, i, j, k) {
+        const V sv = grp_row_t<V>(S, A, p, c, i, j, k);
+        s[c] = sv;
+        acc[0] += (double)sv * (double)p[c];
+      }
+      grp_sum<1>(S, g, acc, s_red);
+      if (threadIdx.x == 0) {
+        if (g->red[0] == 0.0) g->last_x = it;
+        else g->palpha[it] = g->pg / g->red[0];
+      }
+      __syncthreads();
+    }
+  }
+  const int last_x = g->last_x;
+  const V al = (V)g->palpha[kk - 1];
+  #pragma unroll 4
+  GRP_ELEMS(S, g, e) {
+    double y;
+    if (last_x == 0) y = 0.0;
+    else if (kk <= last_x) y = (double)((kk == 1 ? V(0) : x[e]) + al * p[e]);
+    else y = (double)x[e];
+    out[e] = add ? add[e] + y : y;
+  }
+  grp_barrier(S, g);
 }
 
 // out = add + B(v) on the CTA's cells (v and add: this CTA's own cells, already
@@ -304,117 +454,8 @@ __device__ void grp_pc(const GrpSys& S, GrpCta* g, const double* v, double* out,
     grp_barrier(S, g);
     return;
   }
-  const int64_t n = S.n;
-  double* r = S.pcws;
-  double* p = r + n;
-  double* s = p + n;
-  double* x = s + n;
-  const double* dinv = S.dinv;
-  const int kk = P.pc_inner;
-  {
-    // r_0 = v; gamma_0 = <D^-1 r_0, r_0>
-    double acc[1] = {0.0};
-    #pragma unroll 4
-    GRP_ELEMS(S, g, e) {
-      const double rv = v[e];
-      r[e] = rv;
-      acc[0] += (dinv[e] * rv) * rv;
-    }
-    grp_sum<1>(S, g, acc, s_red);
-    if (threadIdx.x == 0) {
-      g->pg = g->red[0];
-      g->last_x = g->pg == 0.0 ? 0 : kk;
-    }
-    __syncthreads();
-  }
-  if (g->last_x > 0) {
-    // p_0 = D^-1 r_0, s_0 = A p_0, eta_0 = <s_0, p_0>
-    #pragma unroll 4
-    GRP_ELEMS(S, g, e) p[e] = dinv[e] * r[e];
-    grp_barrier(S, g);
-    double acc[1] = {0.0};
-    #pragma unroll 2
-    GRP_ROWS(S, g, c, i, j, k) {
-      const double sv = grp_row(S, p, c, i, j, k);
-      s[c] = sv;
-      acc[0] += sv * p[c];
-    }
-    grp_sum<1>(S, g, acc, s_red);
-    if (threadIdx.x == 0) {
-      if (g->red[0] == 0.0) g->last_x = 0;
-      else g->palpha[0] = g->pg / g->red[0];
-    }
-    __syncthreads();
-  }
-  for (int it = 1; it < kk; ++it) {
-    if (it > g->last_x) break;
-    {
-      // r_i = r_{i-1} - alpha_{i-1} s_{i-1}; gamma_i
-      const double al = g->palpha[it - 1];
-      double acc[1] = {0.0};
-      #pragma unroll 4
-      GRP_ELEMS(S, g, e) {
-        const double rv = r[e] - al * s[e];
-        r[e] = rv;
-        acc[0] += (dinv[e] * rv) * rv;
-      }
-      grp_sum<1>(S, g, acc, s_red);
-      if (threadIdx.x == 0) {
-        const double gn = g->red[0];
-        if (gn == 0.0) {
-          g->last_x = it;
-        } else {
-          g->pbeta = gn / g->pg;
-          g->pg = gn;
-        }
-      }
-      __syncthreads();
-    }
-    {
-      // x_i = x_{i-1} + alpha_{i-1} p_{i-1}; p_i = D^-1 r_i + beta_i p_{i-1}
-      const double al = g->palpha[it - 1];
-      const double be = g->pbeta;
-      const bool do_p = it < g->last_x;
-      #pragma unroll 4
-      GRP_ELEMS(S, g, e) {
-        const double po = p[e];
-        x[e] = (it == 1 ? 0.0 : x[e]) + al * po;
-        if (do_p) p[e] = dinv[e] * r[e] + be * po;
-      }
-      if (!do_p) {
-        __syncthreads();
-        break;
-      }
-      grp_barrier(S, g);
-    }
-    {
-      // s_i = A p_i, eta_i
-      double acc[1] = {0.0};
-      #pragma unroll 2
-      GRP_ROWS(S, g, c, i, j, k) {
-        const double sv = grp_row(S, p, c, i, j, k);
-        s[c] = sv;
-        acc[0] += sv * p[c];
-      }
-      grp_sum<1>(S, g, acc, s_red);
-      if (threadIdx.x == 0) {
-        if (g->red[0] == 0.0) g->last_x = it;
-        else g->palpha[it] = g->pg / g->red[0];
-      }
-      __syncthreads();
-    }
-  }
-  const int last_x = g->last_x;
-  const double al = g->palpha[kk - 1];
-  #pragma unroll 4
-  GRP_ELEMS(S, g, e) {
-    double y;
-    if (last_x == 0) y = 0.0;
-    else if (kk <= last_x) y = (kk == 1 ? 0.0 : x[e]) + al * p[e];
-    else y = x[e];
-    out[e] = add ? add[e] + y : y;
-  }
-  grp_barrier(S, g);
+  if (P.pc_fp32) grp_pcg<float>(S, g, GrpCoef<float>{S.d32, S.kx32, S.ky32, S.kz32, S.dinv32}, v, out, add, s_red);
+  else grp_pcg<double>(S, g, grp_coef64(S), v, out, add, s_red);
 }
 
 __device__ __forceinline__ double grp_rho(const GrpParams& P, double gamma, double rr) {
@@ -1253,9 +1294,9 @@ bool group_method_eligible(const pfk_pc_desc* pcd, const pfk_solve_params* prm, 
     w = "the grouped solve runs PFK_PIPEFCG, PFK_PIPEGCR or PFK_PIPEFGMRES";
   else if (prm->mmax < 1 || prm->mmax > PFK_MAX_MMAX) w = "mmax out of range";
   else if (pcd && !(pcd->kind == PFK_PC_NONE || pcd->kind == PFK_PC_JACOBI ||
-                    (pcd->kind == PFK_PC_INNER_PCG && pcd->precision == PFK_FP64 && pcd->inner_iters >= 1 &&
-                     pcd->inner_iters <= kGrpMaxInner)))
-    w = "the grouped solve supports NONE, JACOBI and FP64 INNER_PCG preconditioners";
+                    (pcd->kind == PFK_PC_INNER_PCG && (pcd->precision == PFK_FP64 || pcd->precision == PFK_FP32) &&
+                     pcd->inner_iters >= 1 && pcd->inner_iters <= kGrpMaxInner)))
+    w = "the grouped solve supports NONE, JACOBI and FP64 / FP32 INNER_PCG preconditioners";
   if (why) *why = w;
   return w == nullptr;
 }
@@ -1395,6 +1436,11 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
     }
   if (slot < 0) return PFK_ERR_BUSY;
   const int64_t n = op->n;
+  const bool fp32 = pcd && pcd->kind == PFK_PC_INNER_PCG && pcd->precision == PFK_FP32;
+  if (fp32) {
+    const pfk_status cs = ensure_reduced_copies(const_cast<pfk_operator*>(op), PFK_FP32);
+    if (cs != PFK_OK) return cs;
+  }
   void* mem = nullptr;
   cudaError_t e = cudaMallocAsync(&mem, workspace_bytes(n, prm->mmax, nblk), M.st);
   if (e == cudaErrorMemoryAllocation) {
@@ -1406,6 +1452,7 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
   GrpSys S{};
   S.nx = op->nx; S.ny = op->ny; S.nz = op->nz; S.ndim = op->ndim; S.n = n;
   S.d = op->d; S.kx = op->kx; S.ky = op->ky; S.kz = op->kz; S.dinv = op->dinv;
+  S.d32 = op->d32; S.kx32 = op->kx32; S.ky32 = op->ky32; S.kz32 = op->kz32; S.dinv32 = op->dinv32;
   S.a0 = op->adv[0]; S.a1 = op->adv[1]; S.a2 = op->adv[2];
   S.u0 = op->upw[0]; S.u1 = op->upw[1]; S.u2 = op->upw[2];
   S.adv = op->adv[0] != 0.0 || op->adv[1] != 0.0 || op->adv[2] != 0.0;
@@ -1425,6 +1472,7 @@ pfk_status GroupRunner::admit(const pfk_operator* op, const pfk_pc_desc* pcd, co
   P.rtol = prm->rtol; P.atol = prm->atol;
   P.pc_kind = pcd ? pcd->kind : PFK_PC_NONE;
   P.pc_inner = pcd ? pcd->inner_iters : 0;
+  P.pc_fp32 = fp32 ? 1 : 0;
   P.sigma = prm->sigma;
   P.bar_timeout_ns = prm->barrier_timeout_us == 0 ? 2000000000LL
                      : prm->barrier_timeout_us < 0 ? 0LL

@@ -7,8 +7,8 @@
 namespace pfk {
 
 // Whether a system can run on the grouped kernel (stencil operator, PIPEFCG,
-// PIPEGCR or PIPEFGMRES, NONE / JACOBI / FP64 INNER_PCG preconditioner); *why
-// says why not.
+// PIPEGCR or PIPEFGMRES, NONE / JACOBI / FP64 or FP32 INNER_PCG
+// preconditioner); *why says why not.
 bool group_eligible(const pfk_operator* op, const pfk_pc_desc* pc, const pfk_solve_params* prm, const char** why);
 // The method and preconditioner part of that test alone.
 bool group_method_eligible(const pfk_pc_desc* pc, const pfk_solve_params* prm, const char** why);

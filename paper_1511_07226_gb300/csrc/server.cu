@@ -2,7 +2,7 @@
 //
 // Requests are copied at submission and queued in arrival order.  Requests
 // the grouped kernel can run (stencil, PIPEFCG / PIPEGCR / PIPEFGMRES, NONE /
-// JACOBI / FP64 inner-PCG preconditioner) with at most group_max_n unknowns go to the group queue:
+// JACOBI / inner-PCG preconditioner) with at most group_max_n unknowns go to the group queue:
 // one scheduler thread with its own stream and pfk_context keeps them in a
 // GroupRunner, each with its own group of CTAs, and advances all of them by a
 // few steps per cooperative launch; between launches it publishes the

@@ -460,14 +460,14 @@ def solve_batched(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_it
     return xs, out, hs
 
 
-def solve_grouped(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_iters=4, history: int = 0,
-                  ctas_per_system: int = 0, **kw):
+def solve_grouped(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_iters=4, precision="fp64",
+                  history: int = 0, ctas_per_system: int = 0, **kw):
     """Solves independent stencil systems ops[j] x_j = bs[j] with PIPEFCG,
     PIPEGCR or PIPEFGMRES (method=...) on the grouped persistent kernel (a
     group of CTAs per system, the systems sharing cooperative launches;
     ctas_per_system 1..64, 0 = about one per 4,096 cells, -1 = chosen by
-    timing and cached).  bs / x0s are NumPy arrays (host path); the
-    preconditioner is FP64.  Returns (xs, infos, histories)."""
+    timing and cached).  bs / x0s are NumPy arrays (host path); the inner PCG
+    runs in FP64 or FP32 (precision).  Returns (xs, infos, histories)."""
     lib = load()
     nsys = len(ops)
     prm = make_params(**kw)
@@ -479,7 +479,7 @@ def solve_grouped(ctx: Context, ops, bs, x0s=None, pc_kind="inner_pcg", inner_it
     d = PcDesc()
     d.kind = PC_KINDS[pc_kind]
     d.inner_iters = int(inner_iters)
-    d.precision = PRECISIONS["fp64"]
+    d.precision = PRECISIONS[precision]
     bh = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
     xs = [np.zeros_like(b) if x0s is None else np.array(x0s[j], dtype=np.float64, copy=True)
           for j, b in enumerate(bh)]

@@ -184,6 +184,30 @@ def test_grouped_composition_and_cta_count(ctx):
     assert np.allclose(h2[0][:k, 0], hists[0][:k, 0], rtol=1e-11, atol=0.0)
 
 
+def test_grouped_fp32_inner_pcg(ctx):
+    """FP32 inner Jacobi-PCG (FP32 vectors and coefficient copies) under the
+    FP64 recurrences on the grouped kernel: the leading history against the
+    oracle's FP32 emulation (FP32 rounding order differs), the whole solve to
+    the FP64 true-residual tolerance, and a system's result independent of
+    the batch (bitwise)."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 120 + j) for j, d in enumerate([(20, 18, 16), (24, 16, 12), (16, 16, 16)])]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    kw = dict(pc_kind="inner_pcg", inner_iters=4, precision="fp32", history=3000, ctas_per_system=3, mmax=30,
+              rtol=1e-8, maxit=2000, max_restarts=50)
+    xs, infos, hists = pfk.solve_grouped(ctx, ops, [c["b"] for c in cs], **kw)
+    for c, info, h, x in zip(cs, infos, hists, xs):
+        aop = O.StencilOperator(c["dims"], c["eta"])
+        ref = K.solve("pipefcg", aop, PC.InnerPCG(aop, 4, precision="fp32"), c["b"],
+                      prm=K.Params(mmax=30, rtol=1e-8, maxit=3))
+        rho = ref.rho()
+        assert np.allclose(h[:len(rho), 0], rho, rtol=1e-5, atol=0.0)
+        assert info["status_name"] == "ok"
+        assert np.linalg.norm(c["b"] - aop.apply(x)) <= 1e-8 * np.linalg.norm(c["b"]) * (1 + 1e-6)
+    x1, i1, h1 = pfk.solve_grouped(ctx, [ops[1]], [cs[1]["b"]], **kw)
+    assert np.array_equal(x1[0], xs[1]) and np.array_equal(h1[0], hists[1], equal_nan=True)
+
+
 def test_grouped_tuned_group_size(ctx):
     """ctas_per_system = -1: the group size is chosen by timing trials (x
     restored afterwards) and cached; the solve then equals, bit for bit, the
