@@ -26,7 +26,7 @@ counts and the true relative residual.  tests/test_gpu_headline.py checks the
 GPU's iteration count against the range when its inputs hash the same.
 
 Usage: python tests/golden/make_oracle_spread.py --n 64 --methods pipefcg
-       [--orders numpy,pairwise,reversed,fsum,fma,rowsum] [--workers 6]
+       [--orders numpy,pairwise,reversed,fsum,fma,rowsum] [--workers 6] [--suffix _x]
 (the correlation length is scaled with the grid: ell = 8 n / 128 cells)
 """
 from __future__ import annotations
@@ -70,6 +70,7 @@ def main():
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--max-restarts", type=int, default=200)
     ap.add_argument("--workers", type=int, default=6)
+    ap.add_argument("--suffix", default="", help="appended to the output file name")
     args = ap.parse_args()
     spec = field(args.n)
     prm = dict(mmax=30, rtol=1e-8, maxit=args.maxit, max_restarts=args.max_restarts)
@@ -88,7 +89,7 @@ def main():
                "generator": "tests/golden/make_oracle_spread.py (oracle/ only)",
                "runs": mine,
                "converged_iterations": {"min": min(its), "max": max(its)} if its else None}
-        with open(spread_path(args.n, m), "w") as fh:
+        with open(spread_path(args.n, m)[:-5] + args.suffix + ".json", "w") as fh:
             json.dump(doc, fh, indent=1)
             fh.write("\n")
         print(json.dumps({"method": m, "runs": [(r["order"], r["status"], r["iterations"], r["restarts"])
