@@ -468,8 +468,11 @@ pfk_status pfk_submit(pfk_server* srv, const pfk_request* req, uint64_t* ticket)
 /* Waits up to wait_ms (< 0: without limit) for the request.  PFK_PENDING if it
  * is not done yet; otherwise the solve's status, with x_out (host, length n;
  * may be NULL), info (may be NULL) and latency_ms = submission to completion
- * (may be NULL) filled in, and the ticket released.  PFK_ERR_INVALID for an
- * unknown or already collected ticket. */
+ * (may be NULL) filled in, and the ticket released.  For a request served on
+ * the grouped kernel info->time_ms is the host time from its admission to its
+ * completion (its launches are shared with other requests) and
+ * info->pass_launches its CTA count.  PFK_ERR_INVALID for an unknown or
+ * already collected ticket. */
 pfk_status pfk_poll(pfk_server* srv, uint64_t ticket, double* x_out, pfk_solve_info* info, double* latency_ms,
                     int wait_ms);
 /* Stops admitting, finishes the active solves, drops queued requests. */
