@@ -286,6 +286,27 @@ def test_grouped_barrier_timeout_is_reported(ctx):
     assert infos[0]["status"] == 0
 
 
+def test_server_grouped_request_barrier_timeout(ctx):
+    """A served grouped request whose system barrier may not wait
+    (barrier_timeout_us < 0, 4 CTAs) ends with PFK_ERR_TIMEOUT through the
+    server; requests before and after it are served normally."""
+    from paper_1511_07226_gb300 import pfk
+    c = _cube((24, 24, 24), 130)
+    kw = dict(mmax=30, rtol=1e-8, maxit=2000)
+    srv = pfk.Server(ctx, workers=1)
+    try:
+        t0 = srv.submit(c["dims"], c["eta"], c["b"], **kw)
+        t1 = srv.submit(c["dims"], c["eta"], c["b"], barrier_timeout_us=-1, **kw)
+        assert srv.poll(t0)[1]["status_name"] == "ok"
+        with pytest.raises(pfk.PfkError, match="timed out"):
+            srv.poll(t1)
+        t2 = srv.submit(c["dims"], c["eta"], c["b"], **kw)
+        x2, i2, _ = srv.poll(t2)
+        assert i2["status_name"] == "ok" and i2["pass_launches"] == 4
+    finally:
+        srv.close()
+
+
 def test_server_grouped_requests_bitwise_and_oracle(ctx):
     """Requests served together through the grouped path (PIPEFCG, PIPEGCR,
     PIPEFGMRES up to group_max_n unknowns) equal, bit for bit, the same
