@@ -278,7 +278,8 @@ def main():
                     help="threads per block of the --case batched profiler case")
     ap.add_argument("--extras", default="config1,fcg,pipegcr,nu_sweep,stokes,batched,grouped,fgmres256,serve,serve_sweep",
                     help="comma-separated secondary measurements (config1, fcg, pipegcr, nu_sweep, stokes, batched, "
-                         "grouped, fgmres256, serve, serve_sweep) or 'none'")
+                         "grouped, fgmres256, serve, serve_sweep; grouped_sweep is not in the default list) or "
+                         "'none'")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
@@ -946,6 +947,36 @@ def extra_grouped(ctx, dev, args) -> dict:
             "fp64_peak_note": "FP64 FMA-chain probe (pfk_probe_fp64_fma) run in this leg, FLOP/s / 2", "runs": rows}
 
 
+def extra_grouped_sweep(ctx, dev, args) -> dict:
+    """CTAs per system on the grouped kernel (not in the default run): per side
+    16-64 and cells per CTA 1,024-16,384, as many systems as one launch holds
+    (at most 128) run up to 60 PIPEFCG iterations (as in `grouped`); the
+    launch's system-iterations per second, and the time per iteration of one
+    system alone."""
+    import workloads as W
+    from paper_1511_07226_gb300 import pfk
+    kw = dict(pc_kind="inner_pcg", inner_iters=4, mmax=30, rtol=1e-300, maxit=60, max_restarts=0)
+    rows = []
+    for side in (16, 24, 32, 40, 48, 64):
+        n = side ** 3
+        for cells in (1024, 2048, 4096, 8192, 16384):
+            c = max(1, min(64, -(-n // cells)))
+            count = max(1, min(128, (3 * 152) // c))
+            ps = [W.poisson3d_gaussian(n=side, ell=4.0, log_contrast=2.0, config_id=5, item_id=700 + j)
+                  for j in range(count)]
+            ops = [pfk.Operator.stencil(ctx, p["dims"], p["eta"]) for p in ps]
+            bs = [p["b"] for p in ps]
+            pfk.solve_grouped(ctx, ops[:1], bs[:1], ctas_per_system=c, **kw)
+            _, gi, _ = pfk.solve_grouped(ctx, ops, bs, ctas_per_system=c, **kw)
+            _, g1, _ = pfk.solve_grouped(ctx, ops[:1], bs[:1], ctas_per_system=c, **kw)
+            thr = sum(i["iterations"] for i in gi) / (gi[0]["time_ms"] / 1e3)
+            rows.append({"side": side, "cells_per_cta": cells, "ctas": c, "systems": count,
+                         "system_iterations_per_s": thr, "ms_per_iteration_loaded": 1e3 * count / thr,
+                         "ms_per_iteration_alone": g1[0]["time_ms"] / (g1[0]["iterations"] + 1)})
+    return {"workload": "3D contrast 1e4, PIPEFCG nu_max=30, 4 inner FP64 Jacobi-PCG, up to 60 iterations",
+            "runs": rows}
+
+
 def oracle_request_sample(reqs, probs, iterations, count: int = 3) -> dict:
     """The oracle on the `count` smallest requests of the replay: pipeline fill
     plus two iterations timed on one host core, extrapolated to the GPU's
@@ -1007,7 +1038,7 @@ STOKES_N = 256
 STOKES_INNER_RTOL = 1e-3
 STOKES_INNER_MAXIT = 500
 
-EXTRAS = {"grouped": extra_grouped, "config1": extra_config1, "fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "stokes": extra_stokes,
+EXTRAS = {"grouped": extra_grouped, "grouped_sweep": extra_grouped_sweep, "config1": extra_config1, "fcg": extra_fcg, "pipegcr": extra_pipegcr, "nu_sweep": extra_nu_sweep, "stokes": extra_stokes,
           "serve_sweep": extra_serve_sweep, "batched": extra_batched, "fgmres256": extra_fgmres256, "serve": extra_serve}
 
 
