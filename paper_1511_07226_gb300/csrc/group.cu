@@ -1329,9 +1329,9 @@ int group_ctas(int64_t n, int64_t rows, int requested) {
 
 // Cells per CTA chosen by timing (ctas_per_system = -1), per device, size
 // bucket (ceil log2 of the batch's largest system), method and
-// preconditioner; kept for the process.
+// preconditioner (kind, inner iterations, precision); kept for the process.
 static std::mutex g_tuned_mu;
-static std::map<std::tuple<int, int, int, int, int>, int64_t> g_tuned_cells;
+static std::map<std::tuple<int, int, int, int, int, int>, int64_t> g_tuned_cells;
 
 struct GroupRunner::Impl {
   pfk_context* ctx = nullptr;
@@ -1639,7 +1639,8 @@ extern "C" pfk_status pfk_solve_grouped(pfk_context* ctx, int nsys, const pfk_op
     int64_t nmax = 0;
     for (int j = 0; j < nsys; ++j) nmax = std::max(nmax, ops[j]->n);
     const auto key = std::make_tuple(ctx->device, (int)std::ceil(std::log2((double)std::max<int64_t>(nmax, 2))),
-                                     (int)prm->method, pcd ? (int)pcd->kind : 0, pcd ? (int)pcd->inner_iters : 0);
+                                     (int)prm->method, pcd ? (int)pcd->kind : 0, pcd ? (int)pcd->inner_iters : 0,
+                                     pcd ? (int)pcd->precision : 0);
     int64_t cells = 0;
     {
       std::lock_guard<std::mutex> lk(g_tuned_mu);
