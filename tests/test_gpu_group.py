@@ -2,7 +2,9 @@
 the server's grouped path): each system against the oracle (envelope protocol of tests/_parity.py),
 bitwise independence of the batch composition and of the serving order, CTA
 counts from 1 to several per system, the headline regime at 32^3 against the
-stored oracle envelope, and the bounded group barrier's time-out."""
+stored oracle envelope, the bounded group barrier's time-out, and edge cases
+(b = 0, one-cell and one-row grids with more CTAs requested than rows, the
+smallest and largest window)."""
 import numpy as np
 import pytest
 
@@ -348,3 +350,55 @@ def test_server_grouped_requests_bitwise_and_oracle(ctx):
         assert abs(info["iterations"] - ref.iterations) <= band
         err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
         assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("method", ["pipefcg", "pipegcr", "pipefgmres"])
+def test_grouped_zero_rhs(ctx, method):
+    """b = 0, x0 = 0: every system stops in its fill with x = 0 and no
+    iteration, whatever its CTA count."""
+    from paper_1511_07226_gb300 import pfk
+    cs = [_cube(d, 140 + j) for j, d in enumerate([(9, 7, 5), (12, 12, 12)])]
+    ops = [pfk.Operator.stencil(ctx, c["dims"], c["eta"]) for c in cs]
+    xs, infos, _ = pfk.solve_grouped(ctx, ops, [np.zeros(op.n) for op in ops], pc_kind="jacobi",
+                                     ctas_per_system=3, method=method, sigma=1.0, mmax=8, rtol=1e-8)
+    for x, info in zip(xs, infos):
+        assert info["status_name"] == "ok" and info["iterations"] == 0
+        assert np.all(x == 0.0)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1), (37, 1, 1), (1, 29, 1), (1, 1, 41), (33, 1), (70, 3)])
+@pytest.mark.parametrize("method", ["pipefcg", "pipegcr", "pipefgmres"])
+def test_grouped_degenerate_grids(ctx, dims, method):
+    """One cell, one row or column, one pillar, a 70 x 3 strip, all in one
+    batch with 8 CTAs requested (capped at one per x-row): the group's row
+    split, its ragged tails and a one-CTA group against the oracle."""
+    from paper_1511_07226_gb300 import pfk
+    n = int(np.prod(dims))
+    g = W.rng(31, n)
+    eta = np.power(10.0, g.uniform(-1.0, 1.0, size=n))
+    b = g.uniform(-1.0, 1.0, size=n)
+    aop = O.StencilOperator(dims, eta)
+    prm = K.Params(mmax=8, rtol=1e-10, maxit=200, sigma=1.0)
+    ref, alts = oracle_with_envelope(method, aop, lambda: PC.JacobiPC(aop), b, prm)
+    op = pfk.Operator.stencil(ctx, dims, eta)
+    xs, infos, hists = pfk.solve_grouped(ctx, [op], [b], pc_kind="jacobi", history=400, ctas_per_system=8,
+                                         method=method, sigma=1.0, mmax=8, rtol=1e-10, maxit=200)
+    rows = dims[1] * (dims[2] if len(dims) > 2 else 1)
+    assert infos[0]["pass_launches"] == min(8, rows)
+    check_solve(hists[0], infos[0], ref, alts, rtol=1e-10, min_prefix=1)
+    np.testing.assert_allclose(aop.apply(xs[0]), b, rtol=0, atol=1e-8 * np.linalg.norm(b))
+
+
+def test_grouped_window_and_inner_extremes(ctx):
+    """nu_max = 1 (IPCG) with one inner PCG iteration, and the largest window
+    (nu_max = 32) with eight, on the grouped kernel against the oracle."""
+    from paper_1511_07226_gb300 import pfk
+    c = _cube((16, 14, 12), 150)
+    aop = O.StencilOperator(c["dims"], c["eta"])
+    op = pfk.Operator.stencil(ctx, c["dims"], c["eta"])
+    for mmax, inner in ((1, 1), (32, 8)):
+        xs, infos, hists = pfk.solve_grouped(ctx, [op], [c["b"]], pc_kind="inner_pcg", inner_iters=inner,
+                                             history=3000, ctas_per_system=4, mmax=mmax, rtol=1e-8, maxit=2000)
+        ref, alts = oracle_with_envelope("pipefcg", aop, lambda: PC.InnerPCG(aop, inner), c["b"],
+                                         K.Params(mmax=mmax, rtol=1e-8, maxit=2000))
+        check_solve(hists[0], infos[0], ref, alts, rtol=1e-8)
