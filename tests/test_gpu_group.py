@@ -248,15 +248,18 @@ def test_grouped_nonzero_initial_guess_and_restart_truncation(ctx):
         check_solve(h, info, ref, alts, rtol=1e-8)
 
 
+@pytest.mark.parametrize("n", [32, 48])
 @pytest.mark.parametrize("method", ["pipefcg", "pipegcr"])
-def test_grouped_headline_regime_32cube(ctx, method):
-    """The 32^3 headline case (contrast 1e6, 4 inner FP64 Jacobi-PCG, nu_max =
-    30, rtol 1e-8, residual-replacement restarts) on the grouped kernel with the
-    automatic CTA count, against the stored oracle envelope."""
+def test_grouped_headline_regime(ctx, method, n):
+    """The 32^3 and 48^3 headline cases (contrast 1e6, 4 inner FP64
+    Jacobi-PCG, nu_max = 30, rtol 1e-8, residual-replacement restarts) on the
+    grouped kernel with the automatic CTA count (8 and 27), against the stored
+    oracle envelopes; status, band and restarts only where all its roundings
+    agree on the outcome."""
     from paper_1511_07226_gb300 import pfk
     from tests import _oracle_pool as P
     from tests._headline_cases import CASES
-    name = f"{method}_32"
+    name = f"{method}_{n}"
     if P.load_stored(name) is None:
         pytest.skip("no stored envelope for these inputs")
     cs = CASES[name]
@@ -268,9 +271,10 @@ def test_grouped_headline_regime_32cube(ctx, method):
                                          maxit=prm["maxit"], max_restarts=prm["max_restarts"])
     ref, alts = P.envelope_runs(cs["problem"], cs["method"], cs["pc"], prm, orders=cs["orders"], big=cs["big"],
                                 stored=name)()
-    s = check_solve(hists[0], infos[0], ref, alts, rtol=1e-8, check_restarts=True)
+    agree = all(a.status == ref.status for a in alts)
+    s = check_solve(hists[0], infos[0], ref, alts, rtol=1e-8, check_status=agree, check_restarts=True)
     assert s["prefix"] >= 10, s
-    if ref.status == "converged" and all(a.status == "converged" for a in alts):
+    if agree and ref.status == "converged":
         assert infos[0]["status_name"] == "ok"
 
 
