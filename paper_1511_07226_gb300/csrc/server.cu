@@ -276,16 +276,22 @@ void group_main(pfk_server* srv) {
       cudaFreeAsync(act[k].xb, ctx->stream);
       cudaStreamSynchronize(ctx->stream);
       pfk_destroy_operator(act[k].op);
-      publish(srv, act[k].it, (pfk_status)info.status, info, "");
+      const pfk_status st = (pfk_status)info.status;
+      publish(srv, act[k].it, st, info, st == PFK_OK ? "" : "the grouped solve did not converge");
       act[k] = act.back();
       act.pop_back();
     }
   }
+  // a launch failed while stopping: the rest end with its error
+  const std::string err = ctx ? pfk_last_error(ctx) : "no context for grouped requests";
   for (auto& a : act) {
     R.release(a.slot);
     if (a.xb) cudaFreeAsync(a.xb, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     pfk_destroy_operator(a.op);
+    pfk_solve_info info{};
+    info.status = PFK_ERR_CUDA;
+    publish(srv, a.it, PFK_ERR_CUDA, info, err);
   }
 }
 
